@@ -1,0 +1,388 @@
+"""Benchmark of the Wilson-Dirac hopping operator on one GB300 (and replicas).
+
+Default workload: one even-odd hopping half-application (Eq. (1) restricted to
+the even output sites) on a 32^3 x 64 lattice, FP32 storage, 18-real links,
+synthetic SU(3) links exp(i*0.2*H) (seed 2) and a Gaussian spinor.  A step is
+one plq_hopping_eo call; the metric counts 1320 flop per output site.  The
+working set of a step (805 MB of compulsory traffic) is larger than the 129 MB
+L2, so no flush is needed between steps.
+
+Also reported on the same JSON line:
+  * roofline of the hopping kernel against the measured HBM copy bandwidth,
+  * every storage format of the operator (FP64/FP32/FP16, 18/12-real links),
+  * the solver comparison: FP64 CG vs mixed FP32/FP16-inner CG with FP64
+    reliable updates to a true residual of 1e-10 on 24^3 x 48 (kappa 0.120),
+  * e2e: the same operator through plq_hopping_eo_host with pinned host
+    buffers (host->device and device->host copies inside the timed region),
+  * cpu_baseline: the FP64 C oracle (OpenMP site loop) on the host cores.
+
+``--impl reference`` times the CPU oracle alone on a bounded sample of the same
+workload (the paper's code is not available; the oracle is the reference arm).
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no
+collective in the data path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+FLOP_PER_SITE = 1320
+# compulsory bytes per output site of a half-application: the input-parity
+# spinor, the output spinor and the 8 links touching the site, each once
+COMPULSORY = {("f64", 18): 1536, ("f64", 12): 1152, ("f32", 18): 768, ("f32", 12): 576,
+              ("f16", 18): 392, ("f16", 12): 296}
+# literature convention without reuse: 8 neighbour spinors + 8 links + 1 output
+NO_REUSE = {("f64", 18): 8 * 192 + 8 * 144 + 192, ("f32", 18): 8 * 96 + 8 * 72 + 96,
+            ("f32", 12): 8 * 96 + 8 * 48 + 96, ("f16", 12): 8 * 52 + 8 * 24 + 52,
+            ("f16", 18): 8 * 52 + 8 * 36 + 52, ("f64", 12): 8 * 192 + 8 * 96 + 192}
+HOP_DIMS = (64, 32, 32, 32)
+CG_DIMS = (48, 24, 24, 24)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample(U, phi, sites, reps_min=1, seconds=10.0, max_reps=50):
+    """Time the C oracle on `sites` output sites, repeated until ~seconds pass."""
+    from oracle import c_oracle as C
+
+    C.hopping_sites(U, phi, sites[:1024])  # load and warm
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        C.hopping_sites(U, phi, sites)
+        reps += 1
+        el = time.perf_counter() - t0
+        if (el >= seconds and reps >= reps_min) or reps >= max_reps:
+            break
+    return reps, el, C.threads()
+
+
+def output_sites(dims, parity):
+    """Lexicographic indices of the sites of one parity."""
+    T, Lx, Ly, Lz = dims
+    t, z, y, x = np.meshgrid(np.arange(T), np.arange(Lz), np.arange(Ly), np.arange(Lx), indexing="ij")
+    lex = ((t * Lz + z) * Ly + y) * Lx + x
+    return lex[((t + x + y + z) % 2) == parity].astype(np.int64)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    dims = HOP_DIMS
+    U, phi = S.gauge_and_spinor(dims, 0.2, 2)
+    sites = output_sites(dims, 0)
+    sample = sites[: len(sites) // 8]
+    from oracle import c_oracle as C
+
+    for _ in range(args.warmup):
+        C.hopping_sites(U, phi, sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        C.hopping_sites(U, phi, sample)
+    el = time.perf_counter() - t0
+    gflops = FLOP_PER_SITE * len(sample) * args.steps / el / 1e9
+    cores = C.threads()
+    desc = (f"C oracle (Eq. (1) site loop, FP64, OpenMP) on {len(sample)} of the {len(sites)} even output sites "
+            f"of a 32^3x64 half-application per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": gflops, "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "hopping half-apply 32^3x64 (sampled 1/8 of output sites)", "lattice": "32^3x64"},
+        "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": gflops, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+METRIC = "hopping-op GFLOP/s (1320 flop/site, 32^3x64 half-apply, FP32 storage, 18-real links)"
+
+
+# ------------------------------------------------------------------ GPU arm
+def time_hop(ctx, torch, prec, out, inp, steps, warmup, parity=0):
+    for _ in range(warmup):
+        ctx.hopping_eo(parity, out, inp, prec)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(steps):
+        ctx.hopping_eo(parity, out, inp, prec)
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / steps  # ms per launch
+
+
+def roofline_entry(ms, vh, prec_name, reals, peak_gbs):
+    b = COMPULSORY[(prec_name, reals)] * vh
+    gbs = b / (ms * 1e-3) / 1e9
+    return {"ms": ms, "gflops": FLOP_PER_SITE * vh / (ms * 1e-3) / 1e9, "gbs_compulsory": gbs,
+            "frac_of_measured_hbm": gbs / peak_gbs, "frac_of_8tbs": gbs / 8000.0,
+            "gbs_no_reuse_convention": NO_REUSE[(prec_name, reals)] * vh / (ms * 1e-3) / 1e9}
+
+
+def cg_section(torch, local_rank, quick):
+    from paper_1405_0700_gb300 import F16, F32, F64, Context
+
+    dims = CG_DIMS if not quick else (16, 8, 8, 8)
+    kappa = 0.120
+    U, b = S.gauge_and_spinor(dims, 0.3, 3)
+    out = {"lattice": "x".join(map(str, dims[1:])) + "x" + str(dims[0]), "kappa": kappa, "eps": 0.3, "seed": 3,
+           "tol": 1e-10}
+    with Context(dims, device=local_rank) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        ctx.gauge_upload(U, 12, F16)
+        bd = ctx.to_device(b, F64)
+        x = ctx.empty_full(F64)
+        runs = {}
+        for name, method, inner in [("cg_f64", "cg", F64), ("cg_mixed_f32", "cg", F32),
+                                    ("cg_mixed_f16", "cg", F16), ("bicgstab_f64", "bicgstab", F64),
+                                    ("bicgstab_mixed_f32", "bicgstab", F32)]:
+            fn = ctx.cg_solve if method == "cg" else ctx.bicgstab_solve
+            fn(x, bd, kappa, tol=1e-10, inner_prec=inner, raise_on_error=False)  # warm (graphs, workspace)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = fn(x, bd, kappa, tol=1e-10, inner_prec=inner, raise_on_error=False)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            runs[name] = {"seconds": el, "iterations": info.iterations, "reliable_updates": info.n_reliable,
+                          "true_rel_residual": info.true_rel_residual, "status": info.status}
+            log(f"[bench] {name}: {el:.3f}s it={info.iterations} res={info.true_rel_residual:.2e}")
+    out["runs"] = runs
+    f64 = runs["cg_f64"]["seconds"]
+    out["speedup_mixed_f32_vs_f64"] = f64 / runs["cg_mixed_f32"]["seconds"]
+    out["speedup_mixed_f16_vs_f64"] = f64 / runs["cg_mixed_f16"]["seconds"]
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="small lattices (smoke use only)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+
+    from paper_1405_0700_gb300 import F16, F32, F64, Context, lib
+
+    torch.cuda.set_device(local_rank)
+    lib()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    dims = HOP_DIMS if not args.quick else (16, 16, 16, 16)
+    t0 = time.perf_counter()
+    U, phi = S.gauge_and_spinor(dims, 0.2, 2)
+    log(f"[bench] fields generated in {time.perf_counter() - t0:.1f}s")
+    vh = S.volume(dims) // 2
+    peak, peak_kind = peaks()
+
+    ctx = Context(dims, device=local_rank)
+    ctx.gauge_upload(U, 18, F32)
+    full = ctx.to_device(phi, F32)
+    e_in, o_in = ctx.halves(full, F32)
+    out = ctx.empty_half(F32)
+
+    # ---- headline: FP32, 18-real links, even output sites
+    for _ in range(args.warmup):
+        ctx.hopping_eo(0, out, o_in, F32)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        start.record()
+        for _ in range(args.steps):
+            ctx.hopping_eo(0, out, o_in, F32)
+        end.record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = start.elapsed_time(end)
+    if dist:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms = ms_total / args.steps
+    gflops_rank = FLOP_PER_SITE * vh / (ms * 1e-3) / 1e9
+    value = gflops_rank * world
+    head = roofline_entry(ms, vh, "f32", 18, peak)
+
+    # ---- e2e: host buffers through plq_hopping_eo_host
+    host_in = o_in.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        ctx.hopping_eo_host(0, host_out, host_in, F32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.hopping_eo_host(0, host_out, host_in, F32)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": FLOP_PER_SITE * vh / e2e_s / 1e9 * world, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(host_out.numel()),
+           "ms_per_step": e2e_s * 1e3}
+
+    # ---- every storage format
+    variants = {}
+    for pname, prec, reals in [("f32", F32, 18), ("f32", F32, 12), ("f16", F16, 12), ("f16", F16, 18),
+                               ("f64", F64, 18), ("f64", F64, 12)]:
+        ctx.gauge_upload(U, reals, prec)
+        fv = ctx.to_device(phi, prec)
+        _, ov = ctx.halves(fv, prec)
+        outv = ctx.empty_half(prec)
+        n = max(5, min(args.steps, 50 if prec != F64 else 10))
+        msv = time_hop(ctx, torch, prec, outv, ov, n, 3)
+        variants[f"{pname}_{reals}"] = roofline_entry(msv, vh, pname, reals, peak)
+        del fv, outv
+        log(f"[bench] {pname}-{reals}: {msv * 1e3:.1f} us, {variants[f'{pname}_{reals}']['gbs_compulsory']:.0f} GB/s")
+    ctx.close()
+
+    cg = None
+    if not args.no_cg:
+        cg = cg_section(torch, local_rank, args.quick)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        sites = output_sites(dims, 0)
+        reps, el, cores = oracle_sample(U, phi, sites, seconds=10.0)
+        cpu = {"value": FLOP_PER_SITE * len(sites) * reps / el / 1e9, "unit": "GFLOP/s", "cores": cores,
+               "kind": "oracle",
+               "sample": f"C oracle (FP64 Eq. (1) site loop, OpenMP) over all {len(sites)} even output sites of the "
+                         f"same 32^3x64 half-application, {reps} repetitions in {el:.1f}s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "GFLOP/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "hopping half-apply (plq_hopping_eo, even output sites)",
+                       "lattice": "x".join(map(str, dims[1:])) + "x" + str(dims[0]), "links": "18-real FP32",
+                       "spinor": "FP32 SoA", "gauge": "exp(i*0.2*H) seed 2", "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (805 MB compulsory traffic per step), no flush"},
+            "roofline": {"bound": "hbm", "achieved": head["gbs_compulsory"], "peak": peak, "unit": "GB/s",
+                         "frac": head["gbs_compulsory"] / peak, "traffic": None, "peak_kind": peak_kind,
+                         "bytes_per_site": COMPULSORY[("f32", 18)], "frac_of_8tbs": head["frac_of_8tbs"]},
+            "hbm_gbs": head["gbs_compulsory"],
+            "gbs_no_reuse_convention": head["gbs_no_reuse_convention"],
+            "variants": variants,
+            "cg": cg,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * plq.h -- C ABI of the GB300 Wilson-Dirac library (libplq.so).
+ *
+ * The library implements the hot path of "PLQCD library for Lattice QCD on
+ * multi-core machines" (Abdel-Rehim et al., LATTICE 2013): the hopping part of
+ * the Wilson-Dirac operator, Eq. (1),
+ *
+ *   psi(x) = sum_mu [ U_mu(x) (1 - gamma_mu) phi(x + mu)
+ *                     + U_mu(x - mu)^dagger (1 + gamma_mu) phi(x - mu) ],
+ *
+ * evaluated through the two-component half spinors of Eq. (2) and the remark
+ * after it (only the upper two spin components of theta+- are computed), and
+ * the linear solvers that call it.  Every operation runs in CUDA kernels on
+ * one GPU; no call falls back to the CPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * dims[4] = {T, Lx, Ly, Lz}: mu = 0 is time, mu = 1, 2, 3 are x, y, z.  Every
+ *   extent must be even and >= 2.  V = T*Lx*Ly*Lz sites, Vh = V/2 per parity.
+ * Parity of a site = (t + x + y + z) mod 2; parity 0 is "even".
+ * Lexicographic site index: s = ((t*Lz + z)*Ly + y)*Lx + x.  The checkerboard
+ *   index of a site inside its parity is s/2 (integer division; x is fastest
+ *   and Lx is even, so this is a bijection per parity).
+ * Boundary conditions: periodic in x, y, z; a hop that crosses between
+ *   t = T-1 and t = 0 is multiplied by t_bc (-1 = antiperiodic, +1 periodic).
+ *   The sign is applied inside the kernels, never folded into stored links.
+ * gamma basis (chiral, the DD-HMC documentation the paper cites after
+ *   Eq. (2)): gamma_mu = [[0, A_mu], [A_mu^dagger, 0]], A_0 = -1,
+ *   A_k = -i sigma_k, gamma_5 = diag(1, 1, -1, -1).
+ * Wilson operator M = 1 - kappa*H (H exactly as Eq. (1); free-field critical
+ *   kappa = 1/8).  Even-odd Schur complement Mhat = 1 - kappa^2 H_eo H_oe.
+ *
+ * Canonical (user) layouts, interleaved (re, im) FP64:
+ *   spinor  phi[s][spin 0..3][colour 0..2]            24 doubles per site
+ *   gauge   U[s][mu 0..3][row 0..2][col 0..2]         72 doubles per site
+ *
+ * Internal ("packed") layouts, device memory, structure of arrays:
+ *   A half field holds the Vh sites of one parity for nrhs right-hand sides.
+ *   Its components are grouped in 16-byte planes; plane k of site i and
+ *   right-hand side r is element ((k*Vh + i)*nrhs + r).  Complex component
+ *   c = spin*3 + colour.
+ *     PLQ_F64: 12 planes of (re, im) double           192 B per site and rhs
+ *     PLQ_F32:  6 planes of (re0, im0, re1, im1) float  96 B per site and rhs
+ *     PLQ_F16:  3 planes of 8 IEEE binary16 values (4 complex), followed by a
+ *               float plane of per-site norms n = max |real or imaginary
+ *               component|; stored halves are component / n    52 B per site
+ *   A full field is the even half followed by the odd half.
+ *   plq_field_bytes() gives the byte size of one half field.
+ *
+ * Memory ownership: fields passed to the entry points are caller-owned device
+ * buffers (for example PyTorch tensors) unless a parameter says otherwise.
+ * Every device pointer must be 16-byte aligned.  The library owns its packed
+ * copies of the gauge field and its solver workspace, released by
+ * plq_finalize.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Operator calls are asynchronous on that stream.  Solver calls
+ * synchronise it before they return because they fill plq_solve_info.
+ *
+ * Errors: every function returns PLQ_OK (0) or an error code; the matching
+ * message is available from plq_last_error() in the calling thread.  No entry
+ * point traps on the device, asserts, or throws across the ABI.  Invalid
+ * arguments (NULL or misaligned pointers, bad precision, bad parity, nrhs out
+ * of range) return PLQ_ERR_ARG and launch nothing.
+ */
+#ifndef PLQ_H
+#define PLQ_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define PLQ_API __attribute__((visibility("default")))
+#else
+#define PLQ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int plq_status;
+
+enum {
+    PLQ_OK = 0,
+    PLQ_ERR_ARG = 1,           /* invalid argument; nothing was launched          */
+    PLQ_ERR_CUDA = 2,          /* a CUDA runtime call failed                       */
+    PLQ_ERR_NOMEM = 3,         /* device or pinned allocation failed               */
+    PLQ_ERR_NOT_CONVERGED = 4, /* solver hit maxit before reaching tol             */
+    PLQ_ERR_BREAKDOWN = 5,     /* Krylov breakdown (rho or omega vanished)         */
+    PLQ_ERR_NAN = 6,           /* a NaN or Inf appeared in a solver scalar         */
+    PLQ_ERR_TIMEOUT = 7,       /* a device-side wait ran out of its spin limit     */
+    PLQ_ERR_STATE = 8          /* call out of order (e.g. no gauge field uploaded) */
+};
+
+/* Storage precisions of packed fields.  PLQ_F32 and PLQ_F16 compute in FP32;
+ * PLQ_F64 computes in FP64. */
+enum { PLQ_F64 = 0, PLQ_F32 = 1, PLQ_F16 = 2 };
+
+/* Maximum number of right-hand sides of the multi-RHS operator (one link load
+ * serves all of them; 12 = the spin x colour columns of a point source). */
+#define PLQ_MAX_RHS 12
+
+typedef struct plq_ctx plq_ctx;
+
+/* Solver parameters.  Fields left zero take the documented default. */
+typedef struct {
+    double tol;        /* target true relative residual ||b - M x|| / ||b||, default 1e-10 */
+    int maxit;         /* cap on inner Krylov iterations (all restarts), default 20000     */
+    int inner_prec;    /* PLQ_F64 (plain FP64 solve), PLQ_F32 or PLQ_F16 inner precision   */
+    double delta;      /* reliable-update trigger: the FP64 residual is recomputed when the
+                          inner residual fell by this factor since the last update;
+                          default 0.1 (ignored when inner_prec == PLQ_F64)                  */
+    int use_x0;        /* 1: x holds an initial guess on entry (resume); 0: start from 0   */
+    int check_every;   /* inner iterations per host convergence poll, default 16           */
+} plq_solver_params;
+
+/* Per-solve report. */
+typedef struct {
+    int status;               /* same value the call returns                             */
+    int iterations;           /* inner Krylov iterations performed                       */
+    int n_reliable;           /* FP64 residual recomputations (reliable updates)         */
+    double true_rel_residual; /* ||b - M x|| / ||b|| of the returned x, computed in FP64 */
+    double seconds;           /* wall time of the solve on the stream                    */
+    double hop_applications;  /* half-lattice hopping applications launched              */
+} plq_solve_info;
+
+/* Message of the last error in this thread ("" if none).  The pointer stays
+ * valid until the next failing call in the same thread. */
+PLQ_API const char *plq_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+PLQ_API int plq_version(void);
+
+/* Create a context for a lattice on CUDA device `device` (made current for
+ * the calling thread).  dims as described above; t_bc is -1 (antiperiodic
+ * time, the default physics) or +1.  Returns PLQ_ERR_ARG for odd or < 2
+ * extents, volumes above 2^30 sites, or |t_bc| != 1.  *ctx receives the
+ * handle; release it with plq_finalize. */
+PLQ_API plq_status plq_init(plq_ctx **ctx, const int dims[4], int t_bc, int device);
+
+/* Free every device and host resource of the context.  NULL is accepted. */
+PLQ_API plq_status plq_finalize(plq_ctx *ctx);
+
+/* Number of sites of one parity, Vh. */
+PLQ_API long plq_half_volume(const plq_ctx *ctx);
+
+/* Bytes of one packed half field of precision `prec` holding `nrhs`
+ * right-hand sides (0 on bad arguments). */
+PLQ_API size_t plq_field_bytes(const plq_ctx *ctx, int prec, int nrhs);
+
+/* Pack the gauge field into the library-owned copy of precision `prec`
+ * (Eq. (1): U_mu(x) is the link from x to x + mu).
+ *   U          canonical FP64 gauge field (72 doubles per site), host memory
+ *              if is_device == 0 (copied synchronously), device memory if 1.
+ *   link_reals 18 (full 3x3) or 12 (rows 0 and 1; row 2 is rebuilt in the
+ *              kernels as conj(row0 x row1), valid for SU(3) links only).
+ *   prec       PLQ_F64, PLQ_F32 or PLQ_F16 storage of the copy.
+ * Each precision has its own copy; uploading again replaces it.  Solvers need
+ * the PLQ_F64 copy and the copy of their inner precision.  For link_reals ==
+ * 12 every link is checked to be special unitary to 1e-12 (max abs deviation
+ * of U U^dagger from 1 and of row 2 from conj(row0 x row1)); PLQ_ERR_ARG if
+ * not.  Synchronises `stream`. */
+PLQ_API plq_status plq_gauge_upload(plq_ctx *ctx, const double *U, int is_device, int link_reals, int prec, void *stream);
+
+/* Canonical FP64 spinor fields -> packed full field of precision `prec`.
+ *   in   device, `nrhs` canonical fields back to back (nrhs * V * 24 doubles)
+ *   out  device, 2 * plq_field_bytes(prec, nrhs) bytes: the even half field
+ *        then the odd half field, right-hand sides interleaved as described
+ *        above.
+ * Conversion to FP32 / FP16 rounds to nearest; FP16 stores component/norm. */
+PLQ_API plq_status plq_pack_spinor(plq_ctx *ctx, void *out, const double *in, int prec, int nrhs, void *stream);
+
+/* Packed full field of precision `prec` -> `nrhs` canonical FP64 fields. */
+PLQ_API plq_status plq_unpack_spinor(plq_ctx *ctx, double *out, const void *in, int prec, int nrhs, void *stream);
+
+/* Half-lattice hopping operator (Eq. (1) restricted to one output parity):
+ *   out = H_{p,1-p} in,  p = out_parity (0: out even, in odd; 1: out odd, in even)
+ * `in` and `out` are packed half fields of precision `prec` with `nrhs`
+ * right-hand sides (1..PLQ_MAX_RHS); with nrhs > 1 every link is loaded once
+ * for all right-hand sides.  Needs the gauge copy of precision `prec`.
+ * `in` and `out` must not overlap. */
+PLQ_API plq_status plq_hopping_eo(plq_ctx *ctx, int out_parity, void *out, const void *in, int prec, int nrhs, void *stream);
+
+/* Same operation on HOST buffers (packed layout, pinned or pageable): the
+ * input half field is copied to the device, the operator applied and the
+ * result copied back; the stream is synchronised before return.  Uses a
+ * library-owned device staging area. */
+PLQ_API plq_status plq_hopping_eo_host(plq_ctx *ctx, int out_parity, void *out_host, const void *in_host, int prec, int nrhs,
+                               void *stream);
+
+/* Wilson operator on the full lattice: out = M in = in - kappa * H in.
+ * `in` and `out` are packed full fields (even half then odd half) of
+ * precision `prec`, nrhs = 1; they must not overlap. */
+PLQ_API plq_status plq_wilson_apply(plq_ctx *ctx, void *out, const void *in, double kappa, int prec, void *stream);
+
+/* Even-odd Schur operator on even half fields: out = Mhat in =
+ * in - kappa^2 H_eo H_oe in (dagger != 0: Mhat^dagger = gamma5 Mhat gamma5).
+ * `tmp` is a caller-owned odd half field of the same precision. */
+PLQ_API plq_status plq_schur_apply(plq_ctx *ctx, void *out, const void *in, void *tmp, double kappa, int dagger, int prec,
+                           void *stream);
+
+/* Solve M x = b by conjugate gradients on the even-odd preconditioned normal
+ * equations Mhat^dagger Mhat x_e = Mhat^dagger bhat, bhat = b_e + kappa H_eo b_o,
+ * then x_o = b_o + kappa H_oe x_e.  x and b are packed full FP64 fields.
+ * inner_prec PLQ_F32/PLQ_F16 runs the Krylov iteration at that precision with
+ * FP64 reliable updates (residual recomputation and solution accumulation in
+ * FP64).  Converged when ||b - M x|| / ||b|| <= tol, verified in FP64 before
+ * return.  Returns PLQ_ERR_NOT_CONVERGED at maxit (x holds the last iterate). */
+PLQ_API plq_status plq_cg_solve(plq_ctx *ctx, void *x, const void *b, double kappa, const plq_solver_params *params,
+                        plq_solve_info *info, void *stream);
+
+/* Same system solved by BiCGstab on Mhat x_e = bhat (no normal equations).
+ * Returns PLQ_ERR_BREAKDOWN when rho or omega vanish. */
+PLQ_API plq_status plq_bicgstab_solve(plq_ctx *ctx, void *x, const void *b, double kappa, const plq_solver_params *params,
+                              plq_solve_info *info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLQ_H */

@@ -1,0 +1,330 @@
+// C ABI of libplq: context, errors, gauge upload, layout conversion and the
+// operator entry points (hopping, Wilson, Schur).  Solvers live in
+// plq_solvers.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "plq_internal.cuh"
+
+namespace plq {
+
+static thread_local char g_err[512] = "";
+
+plq_status set_error(plq_status code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+plq_status cuda_error(cudaError_t e, const char *what) {
+    return set_error(e == cudaErrorMemoryAllocation ? PLQ_ERR_NOMEM : PLQ_ERR_CUDA, "%s: %s (%s)", what,
+                     cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+plq_status launch_hop_f64(const HopArgs &a, int reals, int epi, cudaStream_t s, int block);
+plq_status launch_hop_f32(const HopArgs &a, int reals, int epi, cudaStream_t s, int block);
+plq_status launch_hop_f16(const HopArgs &a, int reals, int epi, cudaStream_t s, int block);
+
+int hop_default_block(int prec) { return prec == PLQ_F64 ? 128 : 128; }
+
+plq_status launch_hop(const HopArgs &a, int prec, int reals, int epi, cudaStream_t s, int block) {
+    if (block <= 0) block = hop_default_block(prec);
+    switch (prec) {
+    case PLQ_F64: return launch_hop_f64(a, reals, epi, s, block);
+    case PLQ_F32: return launch_hop_f32(a, reals, epi, s, block);
+    case PLQ_F16: return launch_hop_f16(a, reals, epi, s, block);
+    default: return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
+    }
+}
+
+plq_status ensure_work(Ctx *c, size_t bytes) {
+    if (c->work_bytes >= bytes) return PLQ_OK;
+    if (c->work) {
+        cudaFree(c->work);
+        c->work = nullptr;
+        c->work_bytes = 0;
+    }
+    PLQ_CUDA(cudaMalloc(&c->work, bytes));
+    c->work_bytes = bytes;
+    return PLQ_OK;
+}
+
+plq_status ensure_stage(Ctx *c, size_t bytes) {
+    if (c->stage_bytes >= bytes) return PLQ_OK;
+    if (c->stage) {
+        cudaFree(c->stage);
+        c->stage = nullptr;
+        c->stage_bytes = 0;
+    }
+    PLQ_CUDA(cudaMalloc(&c->stage, bytes));
+    c->stage_bytes = bytes;
+    return PLQ_OK;
+}
+
+}  // namespace plq
+
+using namespace plq;
+
+namespace {
+
+bool aligned16(const void *p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+plq_status check_ctx(const plq_ctx *ctx) {
+    if (!ctx) return set_error(PLQ_ERR_ARG, "null context");
+    return PLQ_OK;
+}
+
+plq_status use_device(const plq_ctx *ctx) {
+    PLQ_CUDA(cudaSetDevice(ctx->device));
+    return PLQ_OK;
+}
+
+plq_status need_gauge(const plq_ctx *ctx, int prec) {
+    if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
+    if (!ctx->gauge[prec].ptr)
+        return set_error(PLQ_ERR_STATE, "no gauge field uploaded for precision %d (call plq_gauge_upload)", prec);
+    return PLQ_OK;
+}
+
+HopArgs hop_args(const plq_ctx *ctx, int prec, int out_parity, void *out, const void *in) {
+    HopArgs a;
+    a.in = in;
+    a.out = out;
+    a.gauge = ctx->gauge[prec].ptr;
+    a.gblock = ctx->gauge[prec].block;
+    a.out_parity = out_parity;
+    a.lat = ctx->lat;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *plq_last_error(void) { return g_err; }
+
+int plq_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+plq_status plq_init(plq_ctx **out, const int dims[4], int t_bc, int device) {
+    g_err[0] = 0;
+    if (!out || !dims) return set_error(PLQ_ERR_ARG, "null argument");
+    *out = nullptr;
+    long long V = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2 || (dims[mu] & 1))
+            return set_error(PLQ_ERR_ARG, "dims[%d] = %d: every extent must be even and >= 2", mu, dims[mu]);
+        V *= dims[mu];
+    }
+    if (V > (1LL << 30)) return set_error(PLQ_ERR_ARG, "volume %lld above 2^30 sites", V);
+    if (t_bc != 1 && t_bc != -1) return set_error(PLQ_ERR_ARG, "t_bc must be +1 or -1 (got %d)", t_bc);
+    int ndev = 0;
+    PLQ_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return set_error(PLQ_ERR_ARG, "device %d of %d", device, ndev);
+    PLQ_CUDA(cudaSetDevice(device));
+    plq_ctx *c = new (std::nothrow) plq_ctx();
+    if (!c) return set_error(PLQ_ERR_NOMEM, "host allocation");
+    for (int mu = 0; mu < 4; ++mu) c->lat.L[mu] = dims[mu];
+    c->lat.Vh = (int)(V / 2);
+    c->lat.t_bc = t_bc;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = cudaMalloc(&c->partials, sizeof(double) * 4 * kMaxReduceBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&c->ticket, sizeof(unsigned) * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&c->sums, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&c->state, sizeof(SolverState));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->sums_host, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->state_host, sizeof(SolverState));
+    if (e == cudaSuccess) e = cudaMemset(c->ticket, 0, sizeof(unsigned) * 16);
+    if (e == cudaSuccess) e = cudaMemset(c->state, 0, sizeof(SolverState));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        plq_status st = cuda_error(e, "plq_init allocation");
+        plq_finalize(c);
+        return st;
+    }
+    *out = c;
+    return PLQ_OK;
+}
+
+plq_status plq_finalize(plq_ctx *c) {
+    if (!c) return PLQ_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &g : c->gauge)
+        if (g.ptr) cudaFree(g.ptr);
+    if (c->partials) cudaFree(c->partials);
+    if (c->ticket) cudaFree(c->ticket);
+    if (c->sums) cudaFree(c->sums);
+    if (c->state) cudaFree(c->state);
+    if (c->sums_host) cudaFreeHost(c->sums_host);
+    if (c->state_host) cudaFreeHost(c->state_host);
+    if (c->work) cudaFree(c->work);
+    if (c->stage) cudaFree(c->stage);
+    delete c;
+    return PLQ_OK;
+}
+
+long plq_half_volume(const plq_ctx *c) { return c ? (long)c->lat.Vh : 0; }
+
+size_t plq_field_bytes(const plq_ctx *c, int prec, int nrhs) {
+    if (!c || !valid_prec(prec) || nrhs < 1 || nrhs > PLQ_MAX_RHS) return 0;
+    return spinor_site_bytes(prec) * (size_t)c->lat.Vh * (size_t)nrhs;
+}
+
+plq_status plq_gauge_upload(plq_ctx *c, const double *U, int is_device, int link_reals, int prec, void *stream) {
+    PLQ_TRY(check_ctx(c));
+    if (!U) return set_error(PLQ_ERR_ARG, "null gauge field");
+    if (link_reals != 18 && link_reals != 12) return set_error(PLQ_ERR_ARG, "link_reals must be 18 or 12");
+    if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
+    if (is_device && !aligned16(U)) return set_error(PLQ_ERR_ARG, "gauge pointer not 16-byte aligned");
+    PLQ_TRY(use_device(c));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t V = 2 * (size_t)c->lat.Vh;
+    const size_t canon = V * 72 * sizeof(double);
+    const double *src = U;
+    double *tmp = nullptr;
+    if (!is_device) {
+        PLQ_CUDA(cudaMalloc(&tmp, canon));
+        cudaError_t e = cudaMemcpyAsync(tmp, U, canon, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_error(e, "gauge H2D copy");
+        }
+        src = tmp;
+    }
+    GaugeCopy &g = c->gauge[prec];
+    const size_t block = link_site_bytes(prec, link_reals) * c->lat.Vh;
+    if (g.ptr && (g.block != block)) {
+        cudaStreamSynchronize(s);
+        cudaFree(g.ptr);
+        g.ptr = nullptr;
+    }
+    plq_status st = PLQ_OK;
+    if (!g.ptr) {
+        cudaError_t e = cudaMalloc(&g.ptr, block * 8);
+        if (e != cudaSuccess) {
+            st = cuda_error(e, "gauge allocation");
+            g.ptr = nullptr;
+        }
+    }
+    unsigned *bad = c->ticket + 8;
+    if (st == PLQ_OK) {
+        cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) st = cuda_error(e, "memset");
+    }
+    if (st == PLQ_OK) st = launch_pack_gauge(c->lat, g.ptr, src, prec, link_reals, block, bad, s);
+    unsigned bad_h = 0;
+    if (st == PLQ_OK) {
+        cudaError_t e = cudaMemcpyAsync(&bad_h, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_error(e, "gauge pack");
+    }
+    if (tmp) cudaFree(tmp);
+    if (st != PLQ_OK) return st;
+    if (bad_h) {
+        cudaFree(g.ptr);
+        g = GaugeCopy();
+        return set_error(PLQ_ERR_ARG, "link_reals = 12 needs SU(3) links (deviation above 1e-12)");
+    }
+    g.reals = link_reals;
+    g.block = block;
+    return PLQ_OK;
+}
+
+plq_status plq_pack_spinor(plq_ctx *c, void *out, const double *in, int prec, int nrhs, void *stream) {
+    PLQ_TRY(check_ctx(c));
+    if (!aligned16(out) || !aligned16(in)) return set_error(PLQ_ERR_ARG, "null or misaligned field pointer");
+    if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
+    if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
+    PLQ_TRY(use_device(c));
+    return launch_pack_spinor(c->lat, out, in, prec, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+plq_status plq_unpack_spinor(plq_ctx *c, double *out, const void *in, int prec, int nrhs, void *stream) {
+    PLQ_TRY(check_ctx(c));
+    if (!aligned16(out) || !aligned16(in)) return set_error(PLQ_ERR_ARG, "null or misaligned field pointer");
+    if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
+    if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
+    PLQ_TRY(use_device(c));
+    return launch_unpack_spinor(c->lat, out, in, prec, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+plq_status plq_hopping_eo(plq_ctx *c, int out_parity, void *out, const void *in, int prec, int nrhs, void *stream) {
+    PLQ_TRY(check_ctx(c));
+    if (!aligned16(out) || !aligned16(in)) return set_error(PLQ_ERR_ARG, "null or misaligned field pointer");
+    if (out == in) return set_error(PLQ_ERR_ARG, "in and out must not overlap");
+    if (out_parity != 0 && out_parity != 1) return set_error(PLQ_ERR_ARG, "out_parity must be 0 or 1");
+    if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
+    PLQ_TRY(need_gauge(c, prec));
+    PLQ_TRY(use_device(c));
+    HopArgs a = hop_args(c, prec, out_parity, out, in);
+    a.nrhs = nrhs;
+    return launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, static_cast<cudaStream_t>(stream));
+}
+
+plq_status plq_hopping_eo_host(plq_ctx *c, int out_parity, void *out_host, const void *in_host, int prec, int nrhs,
+                               void *stream) {
+    PLQ_TRY(check_ctx(c));
+    if (!out_host || !in_host) return set_error(PLQ_ERR_ARG, "null host pointer");
+    if (out_parity != 0 && out_parity != 1) return set_error(PLQ_ERR_ARG, "out_parity must be 0 or 1");
+    if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
+    PLQ_TRY(need_gauge(c, prec));
+    PLQ_TRY(use_device(c));
+    const size_t bytes = plq_field_bytes(c, prec, nrhs);
+    PLQ_TRY(ensure_stage(c, 2 * bytes));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *din = static_cast<char *>(c->stage), *dout = din + bytes;
+    PLQ_CUDA(cudaMemcpyAsync(din, in_host, bytes, cudaMemcpyHostToDevice, s));
+    HopArgs a = hop_args(c, prec, out_parity, dout, din);
+    a.nrhs = nrhs;
+    PLQ_TRY(launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s));
+    PLQ_CUDA(cudaMemcpyAsync(out_host, dout, bytes, cudaMemcpyDeviceToHost, s));
+    PLQ_CUDA(cudaStreamSynchronize(s));
+    return PLQ_OK;
+}
+
+plq_status plq_wilson_apply(plq_ctx *c, void *out, const void *in, double kappa, int prec, void *stream) {
+    PLQ_TRY(check_ctx(c));
+    if (!aligned16(out) || !aligned16(in)) return set_error(PLQ_ERR_ARG, "null or misaligned field pointer");
+    if (out == in) return set_error(PLQ_ERR_ARG, "in and out must not overlap");
+    PLQ_TRY(need_gauge(c, prec));
+    PLQ_TRY(use_device(c));
+    const size_t half = plq_field_bytes(c, prec, 1);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const char *ie = static_cast<const char *>(in), *io = ie + half;
+    char *oe = static_cast<char *>(out), *oo = oe + half;
+    // out_e = in_e - kappa H_eo in_o ; out_o = in_o - kappa H_oe in_e
+    HopArgs a = hop_args(c, prec, 0, oe, io);
+    a.x = ie;
+    a.a = -kappa;
+    PLQ_TRY(launch_hop(a, prec, c->gauge[prec].reals, EPI_XPAY, s));
+    HopArgs b = hop_args(c, prec, 1, oo, ie);
+    b.x = io;
+    b.a = -kappa;
+    return launch_hop(b, prec, c->gauge[prec].reals, EPI_XPAY, s);
+}
+
+plq_status plq_schur_apply(plq_ctx *c, void *out, const void *in, void *tmp, double kappa, int dagger, int prec,
+                           void *stream) {
+    PLQ_TRY(check_ctx(c));
+    if (!aligned16(out) || !aligned16(in) || !aligned16(tmp))
+        return set_error(PLQ_ERR_ARG, "null or misaligned field pointer");
+    if (out == in || tmp == in || tmp == out) return set_error(PLQ_ERR_ARG, "in, out and tmp must be distinct");
+    PLQ_TRY(need_gauge(c, prec));
+    PLQ_TRY(use_device(c));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    HopArgs a = hop_args(c, prec, 1, tmp, in);
+    a.dagger = dagger ? 1 : 0;
+    PLQ_TRY(launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s));
+    HopArgs b = hop_args(c, prec, 0, out, tmp);
+    b.dagger = dagger ? 1 : 0;
+    b.x = in;
+    b.a = -kappa * kappa;
+    return launch_hop(b, prec, c->gauge[prec].reals, EPI_XPAY, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,404 @@
+// Device-side access to packed fields: complex arithmetic, spinor and link
+// loads/stores in FP64, FP32 and FP16 storage, and block reductions.
+#pragma once
+
+#include "plq_internal.cuh"
+
+namespace plq {
+
+template <class R>
+struct cx {
+    R re, im;
+};
+
+template <class R>
+__device__ __forceinline__ cx<R> cadd(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> csub(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> cscale(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <class R>
+__device__ __forceinline__ cx<R> cconj(cx<R> a) { return {a.re, -a.im}; }
+
+// a*b + c
+template <class R>
+__device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> b, cx<R> c) {
+    c.re = fma(a.re, b.re, c.re);
+    c.re = fma(-a.im, b.im, c.re);
+    c.im = fma(a.re, b.im, c.im);
+    c.im = fma(a.im, b.re, c.im);
+    return c;
+}
+// conj(a)*b + c
+template <class R>
+__device__ __forceinline__ cx<R> cfma_conj(cx<R> a, cx<R> b, cx<R> c) {
+    c.re = fma(a.re, b.re, c.re);
+    c.re = fma(a.im, b.im, c.re);
+    c.im = fma(a.re, b.im, c.im);
+    c.im = fma(-a.im, b.re, c.im);
+    return c;
+}
+
+// z * i^K for K = 0..3 (+1, +i, -1, -i): no multiplications.
+template <int K, class R>
+__device__ __forceinline__ cx<R> mul_ipow(cx<R> z) {
+    if constexpr ((K & 3) == 0) return z;
+    else if constexpr ((K & 3) == 1) return {-z.im, z.re};
+    else if constexpr ((K & 3) == 2) return {-z.re, -z.im};
+    else return {z.im, -z.re};
+}
+
+// ---------------------------------------------------------------- loads
+// Read-only, L1-cacheable (neighbour spinors are reused by up to 8 sites).
+__device__ __forceinline__ float4 ld_nc(const float4 *p) { return __ldg(p); }
+__device__ __forceinline__ double2 ld_nc(const double2 *p) { return __ldg(p); }
+__device__ __forceinline__ uint4 ld_nc(const uint4 *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_nc(const float *p) { return __ldg(p); }
+// Streaming (evict-first): links are read exactly once per half-apply.
+__device__ __forceinline__ float4 ld_stream(const float4 *p) { return __ldcs(p); }
+__device__ __forceinline__ float2 ld_stream(const float2 *p) { return __ldcs(p); }
+__device__ __forceinline__ double2 ld_stream(const double2 *p) { return __ldcs(p); }
+__device__ __forceinline__ uint4 ld_stream(const uint4 *p) { return __ldcs(p); }
+__device__ __forceinline__ uint2 ld_stream(const uint2 *p) { return __ldcs(p); }
+__device__ __forceinline__ unsigned ld_stream(const unsigned *p) { return __ldcs(p); }
+
+template <int P>
+struct Real_;
+template <>
+struct Real_<PLQ_F64> {
+    using T = double;
+};
+template <>
+struct Real_<PLQ_F32> {
+    using T = float;
+};
+template <>
+struct Real_<PLQ_F16> {
+    using T = float;
+};
+template <int P>
+using RealOf = typename Real_<P>::T;
+
+__device__ __forceinline__ float2 h2f(unsigned u) {
+    __half2 h = *reinterpret_cast<__half2 *>(&u);
+    return __half22float2(h);
+}
+__device__ __forceinline__ unsigned f2h(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<unsigned *>(&h);
+}
+
+// Packed half field: 12 complex components per site and rhs.
+// `stride` = Vh * nrhs (elements of one plane); `e` = site * nrhs + rhs.
+template <int P>
+struct Spinor;
+
+template <>
+struct Spinor<PLQ_F64> {
+    __device__ static void load(const void *base, size_t stride, size_t e, cx<double> v[12]) {
+        const double2 *p = static_cast<const double2 *>(base) + e;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 t = ld_nc(p + k * stride);
+            v[k] = {t.x, t.y};
+        }
+    }
+    __device__ static void store(void *base, size_t stride, size_t e, const cx<double> v[12]) {
+        double2 *p = static_cast<double2 *>(base) + e;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) __stcs(p + k * stride, make_double2(v[k].re, v[k].im));
+    }
+};
+
+template <>
+struct Spinor<PLQ_F32> {
+    __device__ static void load(const void *base, size_t stride, size_t e, cx<float> v[12]) {
+        const float4 *p = static_cast<const float4 *>(base) + e;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 t = ld_nc(p + k * stride);
+            v[2 * k] = {t.x, t.y};
+            v[2 * k + 1] = {t.z, t.w};
+        }
+    }
+    __device__ static void store(void *base, size_t stride, size_t e, const cx<float> v[12]) {
+        float4 *p = static_cast<float4 *>(base) + e;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            __stcs(p + k * stride, make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im));
+    }
+};
+
+template <>
+struct Spinor<PLQ_F16> {
+    // 3 planes of uint4 (8 halves), then stride floats of norms.
+    __device__ static void load(const void *base, size_t stride, size_t e, cx<float> v[12]) {
+        const uint4 *p = static_cast<const uint4 *>(base) + e;
+        const float *nrm = reinterpret_cast<const float *>(static_cast<const uint4 *>(base) + 3 * stride);
+        const float n = ld_nc(nrm + e);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 t = ld_nc(p + k * stride);
+            float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
+            v[4 * k + 0] = {a.x * n, a.y * n};
+            v[4 * k + 1] = {b.x * n, b.y * n};
+            v[4 * k + 2] = {c.x * n, c.y * n};
+            v[4 * k + 3] = {d.x * n, d.y * n};
+        }
+    }
+    __device__ static void store(void *base, size_t stride, size_t e, const cx<float> v[12]) {
+        uint4 *p = static_cast<uint4 *>(base) + e;
+        float *nrm = reinterpret_cast<float *>(static_cast<uint4 *>(base) + 3 * stride);
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 t;
+            t.x = f2h(v[4 * k + 0].re * inv, v[4 * k + 0].im * inv);
+            t.y = f2h(v[4 * k + 1].re * inv, v[4 * k + 1].im * inv);
+            t.z = f2h(v[4 * k + 2].re * inv, v[4 * k + 2].im * inv);
+            t.w = f2h(v[4 * k + 3].re * inv, v[4 * k + 3].im * inv);
+            __stcs(p + k * stride, t);
+        }
+        __stcs(nrm + e, m);
+    }
+};
+
+// ---------------------------------------------------------------- links
+// One (parity, mu) block of Vh links.  Complex element (row, col) = row*3 + col.
+template <int P, int R>
+struct Link;
+
+template <class T>
+__device__ __forceinline__ void reconstruct_row2(cx<T> u[3][3]) {
+    // row2 = conj(row0 x row1): the third row of an SU(3) matrix.
+    u[2][0] = cconj(csub(cfma(u[0][1], u[1][2], cx<T>{0, 0}), cfma(u[0][2], u[1][1], cx<T>{0, 0})));
+    u[2][1] = cconj(csub(cfma(u[0][2], u[1][0], cx<T>{0, 0}), cfma(u[0][0], u[1][2], cx<T>{0, 0})));
+    u[2][2] = cconj(csub(cfma(u[0][0], u[1][1], cx<T>{0, 0}), cfma(u[0][1], u[1][0], cx<T>{0, 0})));
+}
+
+template <int R>
+struct Link<PLQ_F64, R> {
+    __device__ static void load(const void *blk, int Vh, int i, cx<double> u[3][3]) {
+        const double2 *p = static_cast<const double2 *>(blk) + i;
+        constexpr int n = R / 2;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            double2 t = ld_stream(p + (size_t)k * Vh);
+            u[k / 3][k % 3] = {t.x, t.y};
+        }
+        if constexpr (R == 12) reconstruct_row2(u);
+    }
+};
+
+template <>
+struct Link<PLQ_F32, 18> {
+    __device__ static void load(const void *blk, int Vh, int i, cx<float> u[3][3]) {
+        const float4 *p = static_cast<const float4 *>(blk) + i;
+        cx<float> c[9];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float4 t = ld_stream(p + (size_t)k * Vh);
+            c[2 * k] = {t.x, t.y};
+            c[2 * k + 1] = {t.z, t.w};
+        }
+        float2 t = ld_stream(reinterpret_cast<const float2 *>(static_cast<const float4 *>(blk) + 4 * (size_t)Vh) + i);
+        c[8] = {t.x, t.y};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) u[k / 3][k % 3] = c[k];
+    }
+};
+
+template <>
+struct Link<PLQ_F32, 12> {
+    __device__ static void load(const void *blk, int Vh, int i, cx<float> u[3][3]) {
+        const float4 *p = static_cast<const float4 *>(blk) + i;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float4 t = ld_stream(p + (size_t)k * Vh);
+            u[(2 * k) / 3][(2 * k) % 3] = {t.x, t.y};
+            u[(2 * k + 1) / 3][(2 * k + 1) % 3] = {t.z, t.w};
+        }
+        reconstruct_row2(u);
+    }
+};
+
+template <>
+struct Link<PLQ_F16, 18> {
+    // 2 planes of uint4 (complex 0..3, 4..7) + 1 plane of half2 (complex 8)
+    __device__ static void load(const void *blk, int Vh, int i, cx<float> u[3][3]) {
+        const uint4 *p = static_cast<const uint4 *>(blk) + i;
+        cx<float> c[9];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            uint4 t = ld_stream(p + (size_t)k * Vh);
+            float2 a = h2f(t.x), b = h2f(t.y), d = h2f(t.z), e = h2f(t.w);
+            c[4 * k] = {a.x, a.y};
+            c[4 * k + 1] = {b.x, b.y};
+            c[4 * k + 2] = {d.x, d.y};
+            c[4 * k + 3] = {e.x, e.y};
+        }
+        float2 t = h2f(ld_stream(reinterpret_cast<const unsigned *>(static_cast<const uint4 *>(blk) + 2 * (size_t)Vh) + i));
+        c[8] = {t.x, t.y};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) u[k / 3][k % 3] = c[k];
+    }
+};
+
+template <>
+struct Link<PLQ_F16, 12> {
+    // 1 plane of uint4 (complex 0..3) + 1 plane of uint2 (complex 4, 5)
+    __device__ static void load(const void *blk, int Vh, int i, cx<float> u[3][3]) {
+        const uint4 *p = static_cast<const uint4 *>(blk) + i;
+        uint4 t = ld_stream(p);
+        uint2 q = ld_stream(reinterpret_cast<const uint2 *>(static_cast<const uint4 *>(blk) + (size_t)Vh) + i);
+        float2 a = h2f(t.x), b = h2f(t.y), d = h2f(t.z), e = h2f(t.w), f = h2f(q.x), g = h2f(q.y);
+        u[0][0] = {a.x, a.y};
+        u[0][1] = {b.x, b.y};
+        u[0][2] = {d.x, d.y};
+        u[1][0] = {e.x, e.y};
+        u[1][1] = {f.x, f.y};
+        u[1][2] = {g.x, g.y};
+        reconstruct_row2(u);
+    }
+};
+
+// ---------------------------------------------------------------- reductions
+// Reduce NV values per thread over the grid.  Threads first combine in the
+// working precision R inside a warp (cheap on FP32 pipes), warps then combine
+// in FP64 in shared memory and blocks in FP64 through `partials`.  The last
+// block to finish (ticket) adds the partials in block order (deterministic)
+// and returns true with the grid totals in tot[] for thread 0 of that block.
+template <int NV, class R>
+__device__ bool grid_reduce(const Reduce &red, R v[NV], double tot[NV]) {
+    __shared__ double sh[32][NV];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        R x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[warp][k] = (double)x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[w][k];
+            red.partials[blockIdx.x * 4 + k] = s;
+        }
+        __threadfence();
+        unsigned t = atomicAdd(red.ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    // last block: sum partials in block order, split over the threads of a warp
+    if (warp == 0) {
+        for (int k = 0; k < NV; ++k) {
+            double s = 0.0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(red.partials + b * 4 + k);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            tot[k] = s;
+        }
+    }
+    if (threadIdx.x == 0) *red.ticket = 0u;
+    return threadIdx.x == 0;
+}
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// Apply the finalize step of a reduction (thread 0 of the last block): store
+// the grid totals and update the solver scalars in device memory.
+__device__ __forceinline__ void finalize(const Reduce &red, const double *tot, int nv) {
+    for (int k = 0; k < nv; ++k) red.sums[k] = tot[k];
+    SolverState *st = red.st;
+    if (!st) return;
+    switch (red.fin) {
+    case FIN_CG_ALPHA:
+        st->pAp = tot[0];
+        st->alpha = st->rho / tot[0];
+        if (!isfinite(st->alpha)) { st->flags |= FLAG_NAN; st->stop = 1; }
+        break;
+    case FIN_CG_BETA:
+        st->rho_new = tot[0];
+        st->beta = tot[0] / st->rho;
+        st->rho = tot[0];
+        st->iter += 1;
+        if (!isfinite(tot[0])) { st->flags |= FLAG_NAN; st->stop = 1; }
+        else if (tot[0] <= st->stop_r2 || st->iter >= st->maxit) st->stop = 1;
+        break;
+    case FIN_BICG_ALPHA: {
+        st->rv = make_double2(tot[0], tot[1]);
+        const double m = fabs(tot[0]) + fabs(tot[1]);
+        if (!(m > st->tiny)) { st->flags |= (isfinite(m) ? FLAG_BREAKDOWN : FLAG_NAN); st->stop = 1; break; }
+        st->c_alpha = cdiv(st->c_rho, st->rv);
+        break;
+    }
+    case FIN_BICG_OMEGA:
+        st->ts = make_double2(tot[0], tot[1]);
+        st->tt = tot[2];
+        if (!(tot[2] > 0.0) || !finite2(st->ts)) {
+            st->flags |= (isfinite(tot[2]) && finite2(st->ts) ? FLAG_BREAKDOWN : FLAG_NAN);
+            st->stop = 1;
+            break;
+        }
+        st->c_omega = make_double2(tot[0] / tot[2], tot[1] / tot[2]);
+        if (fabs(st->c_omega.x) + fabs(st->c_omega.y) == 0.0) { st->flags |= FLAG_BREAKDOWN; st->stop = 1; }
+        break;
+    case FIN_BICG_RHO: {
+        const double2 rn = make_double2(tot[0], tot[1]);
+        st->r2 = tot[2];
+        st->iter += 1;
+        if (!finite2(rn) || !isfinite(tot[2])) { st->flags |= FLAG_NAN; st->stop = 1; break; }
+        if (tot[2] <= st->stop_r2 || st->iter >= st->maxit) { st->stop = 1; st->c_rho_new = rn; break; }
+        if (!(fabs(rn.x) + fabs(rn.y) > st->tiny * tot[2] * 1e-30)) { st->flags |= FLAG_BREAKDOWN; st->stop = 1; break; }
+        st->c_beta = cmul(cdiv(rn, st->c_rho), cdiv(st->c_alpha, st->c_omega));
+        st->c_rho = rn;
+        st->c_rho_new = rn;
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+// ---------------------------------------------------------------- geometry
+// Coordinates of checkerboard site i of parity `par` (x = 2*(i mod Lx/2) + offset).
+struct SiteGeom {
+    int c[4];     // t, x, y, z
+    int lex;      // lexicographic index
+};
+
+__device__ __forceinline__ SiteGeom site_geom(const Lattice &L, int par, int i) {
+    SiteGeom g;
+    const int Lxh = L.L[1] >> 1;
+    int r = i / Lxh;
+    const int xh = i - r * Lxh;
+    const int y = r % L.L[2];
+    r /= L.L[2];
+    const int z = r % L.L[3];
+    const int t = r / L.L[3];
+    const int x = 2 * xh + ((par + y + z + t) & 1);
+    g.c[0] = t;
+    g.c[1] = x;
+    g.c[2] = y;
+    g.c[3] = z;
+    g.lex = ((t * L.L[3] + z) * L.L[2] + y) * L.L[1] + x;
+    return g;
+}
+
+}  // namespace plq

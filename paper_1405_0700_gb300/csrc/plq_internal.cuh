@@ -1,0 +1,187 @@
+// Internal declarations of libplq: context, packed-field access, kernel
+// parameter blocks and the launchers shared between translation units.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "plq.h"
+
+namespace plq {
+
+// ---------------------------------------------------------------- errors
+plq_status set_error(plq_status code, const char *fmt, ...);
+plq_status cuda_error(cudaError_t e, const char *what);
+
+#define PLQ_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t e__ = (call);                                        \
+        if (e__ != cudaSuccess) return ::plq::cuda_error(e__, #call);    \
+    } while (0)
+
+#define PLQ_TRY(call)                                                    \
+    do {                                                                 \
+        plq_status s__ = (call);                                         \
+        if (s__ != PLQ_OK) return s__;                                   \
+    } while (0)
+
+// ---------------------------------------------------------------- lattice
+struct Lattice {
+    int L[4];   // {T, Lx, Ly, Lz}
+    int Vh;     // sites per parity
+    int t_bc;   // -1 antiperiodic, +1 periodic in time
+};
+
+inline bool valid_prec(int p) { return p == PLQ_F64 || p == PLQ_F32 || p == PLQ_F16; }
+
+// bytes per site and right-hand side of a packed half field
+inline size_t spinor_site_bytes(int prec) { return prec == PLQ_F64 ? 192 : prec == PLQ_F32 ? 96 : 52; }
+
+// bytes per site of one (parity, mu) block of packed links
+inline size_t link_site_bytes(int prec, int reals) {
+    const size_t per_real = prec == PLQ_F64 ? 8 : prec == PLQ_F32 ? 4 : 2;
+    return per_real * (size_t)reals;
+}
+
+struct GaugeCopy {
+    void *ptr = nullptr;
+    int reals = 0;       // 18 or 12; 0 = absent
+    size_t block = 0;    // bytes of one (parity, mu) block
+};
+
+// Device-resident scalars of a Krylov solve.  Kernels read their
+// coefficients from here and the last block of each reduction writes them,
+// so an iteration needs no host round trip (and can be graph-captured).
+struct SolverState {
+    double rho;       // <r, r> (CG) of the previous iteration
+    double rho_new;   // <r, r> just computed
+    double alpha, beta;
+    double pAp;       // ||Mhat p||^2 = <p, Mhat^dag Mhat p>
+    double stop_r2;   // freeze once rho_new <= stop_r2
+    double2 c_rho, c_rho_new, c_alpha, c_omega, c_beta;  // BiCGstab (complex)
+    double2 rv;       // <rhat, v>
+    double2 ts;       // <t, s>
+    double tt;        // <t, t>
+    double r2;        // ||r||^2 (BiCGstab)
+    double tiny;      // breakdown threshold scale
+    int stop;         // 1: converged / triggered; kernels of the iteration return early
+    int iter;         // iterations completed
+    int flags;        // bit 0 NaN, bit 1 breakdown
+    int maxit;        // stop once iter reaches this
+};
+
+enum { FLAG_NAN = 1, FLAG_BREAKDOWN = 2 };
+
+// Reduction of up to 4 doubles per block, combined by the last block to
+// finish (ticket counter), which then applies a finalize step `fin`.
+enum Finalize {
+    FIN_NONE = 0,       // just leave the sums in sums[]
+    FIN_CG_ALPHA,       // pAp = s0; alpha = rho / pAp
+    FIN_CG_BETA,        // rho_new = s0; beta = rho_new / rho; rho = rho_new; iter++; stop test
+    FIN_BICG_ALPHA,     // rv = (s0, s1); alpha = rho_new / rv
+    FIN_BICG_OMEGA,     // ts = (s0, s1); tt = s2; omega = ts / tt
+    FIN_BICG_RHO,       // rho_new = (s0, s1); r2 = s2; beta; iter++; stop test
+};
+
+struct Reduce {
+    double *partials = nullptr;   // >= 4 * gridDim.x doubles
+    unsigned *ticket = nullptr;   // zero on entry, left zero on exit
+    double *sums = nullptr;       // 4 doubles: the grid totals
+    SolverState *st = nullptr;    // target of the finalize step
+    int fin = FIN_NONE;
+};
+
+constexpr int kMaxReduceBlocks = 4096;
+
+struct Ctx {
+    Lattice lat{};
+    int device = 0;
+    GaugeCopy gauge[3];
+    // reduction scratch
+    double *partials = nullptr;
+    unsigned *ticket = nullptr;
+    double *sums = nullptr;
+    double *sums_host = nullptr;  // pinned mirror of sums
+    SolverState *state = nullptr;
+    SolverState *state_host = nullptr;  // pinned
+    // solver workspace (allocated on first use, grown as needed)
+    void *work = nullptr;
+    size_t work_bytes = 0;
+    // staging for the host entry points
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    int num_sms = 0;
+};
+
+plq_status ensure_work(Ctx *c, size_t bytes);
+plq_status ensure_stage(Ctx *c, size_t bytes);
+
+// ---------------------------------------------------------------- hopping
+enum Epilogue {
+    EPI_PLAIN = 0,   // out = H in
+    EPI_XPAY = 1,    // out = x + a * H in
+    EPI_XPAY_NORM = 2,  // ... and sum |out|^2
+    EPI_XPAY_DOTW = 3,  // ... and sum <w, out> (complex)
+    EPI_XPAY_TS = 4,    // ... and sum <out, x> (complex), |out|^2
+};
+
+struct HopArgs {
+    const void *in = nullptr;
+    void *out = nullptr;
+    const void *x = nullptr;   // epilogue source (same parity as out)
+    const void *w = nullptr;   // epilogue dot partner
+    const void *gauge = nullptr;
+    size_t gblock = 0;         // bytes of one (parity, mu) gauge block
+    double a = 0.0;
+    int out_parity = 0;
+    int nrhs = 1;
+    int dagger = 0;
+    Lattice lat{};
+    Reduce red{};
+    const SolverState *st = nullptr;  // if set and st->stop, the kernel returns at once
+};
+
+// Launch the hopping kernel for (prec, link reals, epilogue).  block = 0 picks
+// the tuned default.
+plq_status launch_hop(const HopArgs &a, int prec, int reals, int epi, cudaStream_t s, int block = 0);
+
+int hop_default_block(int prec);
+
+// ---------------------------------------------------------------- layouts
+plq_status launch_pack_spinor(const Lattice &lat, void *out, const double *in, int prec, int nrhs, cudaStream_t s);
+plq_status launch_unpack_spinor(const Lattice &lat, double *out, const void *in, int prec, int nrhs, cudaStream_t s);
+plq_status launch_pack_gauge(const Lattice &lat, void *out, const double *in, int prec, int reals, size_t block,
+                             unsigned *bad, cudaStream_t s);
+
+// ---------------------------------------------------------------- blas
+// All vectors are packed half fields of Vh sites (one right-hand side).
+plq_status blas_copy_convert(int Vh, void *dst, int pdst, const void *src, int psrc, cudaStream_t s);
+plq_status blas_zero(int Vh, void *dst, int prec, cudaStream_t s);
+plq_status blas_gamma5(int Vh, void *dst, const void *src, int prec, cudaStream_t s);
+// sum |v|^2 into red.sums (FP64); blocking = false leaves the result on the device
+plq_status blas_norm2(int Vh, const void *v, int prec, const Reduce &red, cudaStream_t s);
+// x += alpha p; r -= alpha q; rho_new = |r|^2 (alpha from state)
+plq_status blas_cg_update(int Vh, void *x, void *r, const void *p, const void *q, int prec, const Reduce &red,
+                          const SolverState *st, cudaStream_t s);
+// p = r + beta p (beta from state)
+plq_status blas_cg_direction(int Vh, void *p, const void *r, int prec, const SolverState *st, cudaStream_t s);
+// dst(F64) += convert(src)
+plq_status blas_accumulate(int Vh, void *dst64, const void *src, int psrc, cudaStream_t s);
+// y = x + a * y for FP64 vectors with host scalar a (setup paths)
+plq_status blas_xpay64(int Vh, const void *x, double a, void *y, cudaStream_t s);
+// BiCGstab kernels
+plq_status blas_bicg_p(int Vh, void *p, const void *r, const void *v, int prec, const SolverState *st,
+                       cudaStream_t s);
+plq_status blas_bicg_s(int Vh, void *sv, const void *r, const void *v, int prec, const SolverState *st,
+                       cudaStream_t s);
+plq_status blas_bicg_update(int Vh, void *x, void *r, const void *p, const void *sv, const void *t,
+                            const void *rhat, int prec, const Reduce &red, const SolverState *st, cudaStream_t s);
+plq_status blas_dot_norm(int Vh, const void *a, const void *b, int prec, const Reduce &red, cudaStream_t s);
+
+}  // namespace plq
+
+struct plq_ctx : public plq::Ctx {};

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libplq.so (the C ABI declared in include/plq.h).
+
+Only argument marshalling happens here: every step of the operator and of the
+solvers runs in the library's CUDA kernels.  PyTorch provides device memory
+(``torch.uint8`` tensors sized by ``field_bytes``) and the current CUDA stream.
+If ``libplq.so`` is missing the import of this module fails: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libplq.so")
+
+PLQ_OK = 0
+PLQ_ERR_ARG = 1
+PLQ_ERR_CUDA = 2
+PLQ_ERR_NOMEM = 3
+PLQ_ERR_NOT_CONVERGED = 4
+PLQ_ERR_BREAKDOWN = 5
+PLQ_ERR_NAN = 6
+PLQ_ERR_TIMEOUT = 7
+PLQ_ERR_STATE = 8
+
+F64, F32, F16 = 0, 1, 2
+MAX_RHS = 12
+SITE_BYTES = {F64: 192, F32: 96, F16: 52}
+PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16}
+
+# Every function declared in include/plq.h, with (restype, argtypes).
+_c_int, _c_double, _vp, _c_long, _c_size = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_long, ctypes.c_size_t
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [
+        ("tol", ctypes.c_double),
+        ("maxit", ctypes.c_int),
+        ("inner_prec", ctypes.c_int),
+        ("delta", ctypes.c_double),
+        ("use_x0", ctypes.c_int),
+        ("check_every", ctypes.c_int),
+    ]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("iterations", ctypes.c_int),
+        ("n_reliable", ctypes.c_int),
+        ("true_rel_residual", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+        ("hop_applications", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+SIGNATURES = {
+    "plq_last_error": (ctypes.c_char_p, []),
+    "plq_version": (_c_int, []),
+    "plq_init": (_c_int, [ctypes.POINTER(_vp), _vp, _c_int, _c_int]),
+    "plq_finalize": (_c_int, [_vp]),
+    "plq_half_volume": (_c_long, [_vp]),
+    "plq_field_bytes": (_c_size, [_vp, _c_int, _c_int]),
+    "plq_gauge_upload": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _vp]),
+    "plq_pack_spinor": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
+    "plq_unpack_spinor": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
+    "plq_hopping_eo": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _c_int, _vp]),
+    "plq_hopping_eo_host": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _c_int, _vp]),
+    "plq_wilson_apply": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, _vp]),
+    "plq_schur_apply": (_c_int, [_vp, _vp, _vp, _vp, _c_double, _c_int, _c_int, _vp]),
+    "plq_cg_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
+    "plq_bicgstab_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams),
+                                    ctypes.POINTER(SolveInfo), _vp]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libplq.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"{LIB_PATH} is missing: build it with paper_1405_0700_gb300._build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PLQError(RuntimeError):
+    def __init__(self, status, message, info=None):
+        super().__init__(f"plq status {status}: {message}")
+        self.status = status
+        self.info = info
+
+
+def last_error():
+    return lib().plq_last_error().decode()
+
+
+def check(status, info=None):
+    if status != PLQ_OK:
+        raise PLQError(status, last_error(), info)
+    return status
+
+
+def _ptr(t):
+    """Device (or host) address of a torch tensor or numpy array."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+
+    return torch.cuda.current_stream().cuda_stream
+
+
+def prec_of(p):
+    return PREC_NAMES[p] if isinstance(p, str) else int(p)
+
+
+class Context:
+    """A lattice on one GPU: ``dims = (T, Lx, Ly, Lz)``, time boundary ``t_bc``."""
+
+    def __init__(self, dims, t_bc=-1, device=0):
+        self.dims = tuple(int(d) for d in dims)
+        self.t_bc = t_bc
+        self.device = device
+        h = _vp()
+        arr = (ctypes.c_int * 4)(*self.dims)
+        check(lib().plq_init(ctypes.byref(h), ctypes.cast(arr, _vp), t_bc, device))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().plq_finalize(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ sizes
+    @property
+    def half_volume(self):
+        return int(lib().plq_half_volume(self._h))
+
+    @property
+    def volume(self):
+        return 2 * self.half_volume
+
+    def field_bytes(self, prec, nrhs=1):
+        return int(lib().plq_field_bytes(self._h, prec_of(prec), nrhs))
+
+    def empty_half(self, prec, nrhs=1):
+        import torch
+
+        return torch.empty(self.field_bytes(prec, nrhs), dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def empty_full(self, prec, nrhs=1):
+        import torch
+
+        return torch.empty(2 * self.field_bytes(prec, nrhs), dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def halves(self, full, prec, nrhs=1):
+        n = self.field_bytes(prec, nrhs)
+        return full[:n], full[n:]
+
+    # ------------------------------------------------------------ data
+    def gauge_upload(self, U, link_reals=18, prec=F64, stream=None):
+        """U: canonical gauge field (complex128 NumPy array on the host, or a
+        float64/complex128 torch tensor on the device)."""
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.complex128)
+            check(lib().plq_gauge_upload(self._h, U.ctypes.data, 0, link_reals, prec_of(prec), _stream(stream)))
+        else:
+            check(lib().plq_gauge_upload(self._h, U.data_ptr(), 1, link_reals, prec_of(prec), _stream(stream)))
+
+    def pack_spinor(self, out, phi_dev, prec, nrhs=1, stream=None):
+        check(lib().plq_pack_spinor(self._h, _ptr(out), _ptr(phi_dev), prec_of(prec), nrhs, _stream(stream)))
+        return out
+
+    def unpack_spinor(self, out_dev, field, prec, nrhs=1, stream=None):
+        check(lib().plq_unpack_spinor(self._h, _ptr(out_dev), _ptr(field), prec_of(prec), nrhs, _stream(stream)))
+        return out_dev
+
+    def to_device(self, phi, prec, nrhs=1, stream=None):
+        """Canonical complex128 NumPy spinor(s) -> packed full field on the device."""
+        import torch
+
+        src = torch.from_numpy(np.ascontiguousarray(phi, dtype=np.complex128).view(np.float64).ravel())
+        src = src.to(f"cuda:{self.device}")
+        out = self.empty_full(prec, nrhs)
+        self.pack_spinor(out, src, prec, nrhs, stream)
+        return out
+
+    def to_host(self, field, prec, nrhs=1, stream=None):
+        """Packed full field on the device -> canonical complex128 NumPy array."""
+        import torch
+
+        T, Lx, Ly, Lz = self.dims
+        out = torch.empty(nrhs * self.volume * 24, dtype=torch.float64, device=f"cuda:{self.device}")
+        self.unpack_spinor(out, field, prec, nrhs, stream)
+        torch.cuda.synchronize(self.device)
+        a = out.cpu().numpy().view(np.complex128)
+        shape = (T, Lz, Ly, Lx, 4, 3)
+        return a.reshape(((nrhs,) if nrhs > 1 else ()) + shape)
+
+    # ------------------------------------------------------------ operators
+    def hopping_eo(self, out_parity, out, inp, prec, nrhs=1, stream=None):
+        check(lib().plq_hopping_eo(self._h, out_parity, _ptr(out), _ptr(inp), prec_of(prec), nrhs, _stream(stream)))
+        return out
+
+    def hopping_eo_host(self, out_parity, out_host, in_host, prec, nrhs=1, stream=None):
+        check(lib().plq_hopping_eo_host(self._h, out_parity, _ptr(out_host), _ptr(in_host), prec_of(prec), nrhs,
+                                        _stream(stream)))
+        return out_host
+
+    def wilson_apply(self, out, inp, kappa, prec, stream=None):
+        check(lib().plq_wilson_apply(self._h, _ptr(out), _ptr(inp), float(kappa), prec_of(prec), _stream(stream)))
+        return out
+
+    def schur_apply(self, out, inp, tmp, kappa, prec, dagger=False, stream=None):
+        check(lib().plq_schur_apply(self._h, _ptr(out), _ptr(inp), _ptr(tmp), float(kappa), int(bool(dagger)),
+                                    prec_of(prec), _stream(stream)))
+        return out
+
+    # ------------------------------------------------------------ solvers
+    def _solve(self, fn, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every, stream, raise_on_error):
+        p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every)
+        info = SolveInfo()
+        st = fn(self._h, _ptr(x), _ptr(b), float(kappa), ctypes.byref(p), ctypes.byref(info), _stream(stream))
+        if raise_on_error:
+            check(st, info)
+        return info
+
+    def cg_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
+                 check_every=16, stream=None, raise_on_error=True):
+        """CG on the even-odd normal equations; x, b packed full FP64 fields."""
+        return self._solve(lib().plq_cg_solve, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every,
+                           stream, raise_on_error)
+
+    def bicgstab_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
+                       check_every=16, stream=None, raise_on_error=True):
+        """BiCGstab on the even-odd Schur system; x, b packed full FP64 fields."""
+        return self._solve(lib().plq_bicgstab_solve, x, b, kappa, tol, maxit, inner_prec, delta, use_x0,
+                           check_every, stream, raise_on_error)
+
+
+def canonical_gauge_device(U, device=0):
+    """Copy a canonical complex128 NumPy gauge field to the device as float64."""
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(U, dtype=np.complex128).view(np.float64).ravel()).to(f"cuda:{device}")

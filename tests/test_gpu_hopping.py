@@ -1,0 +1,179 @@
+"""GPU hopping operator against the FP64 oracle (Eq. (1)), through the C ABI."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import c_oracle as C
+from oracle import wilson as W
+from gpuhelp import TOL, gpu_hopping_full, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1405_0700_gb300 import F16, F32, F64, Context, PLQError  # noqa: E402
+from paper_1405_0700_gb300 import plq  # noqa: E402
+
+LATTICES = [
+    (2, 2, 2, 2),      # x + mu = x - mu: forward and backward hops hit the same site
+    (4, 4, 4, 4),
+    (8, 8, 8, 8),      # BASELINE config 1 shape
+    (8, 4, 4, 4),      # 4^3 x 8
+    (10, 4, 6, 8),     # anisotropic: catches axis mix-ups
+    (6, 2, 4, 2),      # Vh = 48: a ragged single block
+    (14, 6, 2, 10),    # Vh = 840: several blocks and a ragged tail
+]
+FORMATS = [(F64, 18), (F64, 12), (F32, 18), (F32, 12), (F16, 18), (F16, 12)]
+
+
+@pytest.mark.parametrize("dims", LATTICES)
+@pytest.mark.parametrize("prec,reals", FORMATS)
+def test_hopping_matches_oracle(dims, prec, reals):
+    U, phi = S.gauge_and_spinor(dims, 0.3, 1)
+    ref = W.hopping(U, phi)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, reals, prec)
+        got = gpu_hopping_full(ctx, phi, prec)
+    assert rel(got, ref) <= TOL[prec], (dims, prec, reals, rel(got, ref))
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_periodic_time_boundary(prec):
+    dims = (4, 4, 2, 6)
+    U, phi = S.gauge_and_spinor(dims, 0.3, 2)
+    ref = W.hopping(U, phi, t_bc=+1)
+    with Context(dims, t_bc=+1) as ctx:
+        ctx.gauge_upload(U, 18, prec)
+        got = gpu_hopping_full(ctx, phi, prec)
+    assert rel(got, ref) <= TOL[prec]
+
+
+def test_free_field_plane_wave():
+    # U = 1: H e^{ipx} u = [sum 2cos p - 2i gamma sin p] e^{ipx} u (closed form, independent of the oracle).
+    dims = (8, 4, 6, 4)
+    T, Lx, Ly, Lz = dims
+    shape = S.lattice_shape(dims)
+    U = np.broadcast_to(np.eye(3, dtype=complex), shape + (4, 3, 3)).copy()
+    p = np.array([3 * np.pi / T, 2 * np.pi / Lx, 4 * np.pi / Ly, 6 * np.pi / Lz])
+    t, z, y, x = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    phase = np.exp(1j * (p[0] * t + p[1] * x + p[2] * y + p[3] * z))
+    u = np.random.default_rng(3).standard_normal((4, 3)) + 0j
+    phi = phase[..., None, None] * u
+    K = sum(2 * np.cos(p[m]) * np.eye(4) - 2j * np.sin(p[m]) * W.GAMMA[m] for m in range(4))
+    expect = phase[..., None, None] * (K @ u)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 12, F64)
+        got = gpu_hopping_full(ctx, phi, F64)
+    assert rel(got, expect) < 1e-13
+
+
+@pytest.mark.parametrize("prec", [F64, F32, F16])
+def test_wilson_apply(prec):
+    dims = (8, 4, 4, 4)
+    U, phi = S.gauge_and_spinor(dims, 0.3, 4)
+    kappa = 0.12
+    ref = W.wilson(U, phi, kappa)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, prec)
+        inp = ctx.to_device(phi, prec)
+        out = ctx.empty_full(prec)
+        ctx.wilson_apply(out, inp, kappa, prec)
+        got = ctx.to_host(out, prec)
+    assert rel(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_schur_apply(prec, dagger):
+    dims = (4, 4, 6, 2)
+    U, phi = S.gauge_and_spinor(dims, 0.3, 5)
+    kappa = 0.13
+    v = W.restrict(phi, 0)
+    ref = (W.schur_dag if dagger else W.schur)(U, v, kappa)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, prec)
+        full = ctx.to_device(v, prec)
+        e_in, _ = ctx.halves(full, prec)
+        out = ctx.empty_full(prec)
+        out.zero_()
+        e_out, _ = ctx.halves(out, prec)
+        tmp = ctx.empty_half(prec)
+        ctx.schur_apply(e_out, e_in, tmp, kappa, prec, dagger=dagger)
+        got = ctx.to_host(out, prec)
+    assert rel(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 5, 12])
+@pytest.mark.parametrize("prec,reals", [(F64, 18), (F32, 18), (F32, 12), (F16, 12)])
+def test_multi_rhs(nrhs, prec, reals):
+    dims = (6, 4, 2, 4)
+    U = S.gauge_field(dims, 0.3, 6)
+    phis = np.stack([S.gaussian_spinor(dims, 100 + r) for r in range(nrhs)])
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, reals, prec)
+        got = gpu_hopping_full(ctx, phis if nrhs > 1 else phis[0], prec, nrhs)
+    got = got.reshape((nrhs,) + phis.shape[1:])
+    for r in range(nrhs):
+        assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
+
+
+def test_host_entry_point_matches_device():
+    dims = (8, 4, 4, 4)
+    U, phi = S.gauge_and_spinor(dims, 0.3, 7)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F32)
+        full = ctx.to_device(phi, F32)
+        e_in, o_in = ctx.halves(full, F32)
+        dev_out = ctx.empty_half(F32)
+        ctx.hopping_eo(0, dev_out, o_in, F32)
+        host_in = o_in.cpu().pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        ctx.hopping_eo_host(0, host_out, host_in, F32)
+        torch.cuda.synchronize()
+        assert torch.equal(host_out, dev_out.cpu())
+
+
+def test_errors_are_reported_not_faulted():
+    dims = (4, 4, 4, 4)
+    with Context(dims) as ctx:
+        buf = ctx.empty_half(F32)
+        buf2 = ctx.empty_half(F32)
+        with pytest.raises(PLQError) as e:
+            ctx.hopping_eo(0, buf, buf2, F32)  # no gauge uploaded
+        assert e.value.status == plq.PLQ_ERR_STATE
+        U = S.gauge_field(dims, 0.3, 1)
+        ctx.gauge_upload(U, 18, F32)
+        with pytest.raises(PLQError) as e:
+            ctx.hopping_eo(2, buf, buf2, F32)
+        assert e.value.status == plq.PLQ_ERR_ARG
+        with pytest.raises(PLQError) as e:
+            ctx.hopping_eo(0, buf, buf, F32)
+        assert e.value.status == plq.PLQ_ERR_ARG
+        with pytest.raises(PLQError) as e:
+            ctx.hopping_eo(0, buf[1:], buf2, F32)  # misaligned
+        assert e.value.status == plq.PLQ_ERR_ARG
+        with pytest.raises(PLQError) as e:
+            ctx.hopping_eo(0, buf, buf2, F32, nrhs=13)
+        assert e.value.status == plq.PLQ_ERR_ARG
+        # 12-real storage needs SU(3) links
+        bad = U.copy()
+        bad[0, 0, 0, 0, 1] *= 1.5
+        with pytest.raises(PLQError) as e:
+            ctx.gauge_upload(bad, 12, F32)
+        assert e.value.status == plq.PLQ_ERR_ARG
+        torch.cuda.synchronize()
+
+
+def test_full_size_32c64_sampled_sites():
+    """32^3 x 64 (the benchmark workload) in the benchmark's launch configuration,
+    checked at sampled output sites computed one by one by the C oracle."""
+    dims = (64, 32, 32, 32)
+    U, phi = S.gauge_and_spinor(dims, 0.2, 2)
+    V = S.volume(dims)
+    rng = np.random.default_rng(0)
+    sites = np.concatenate([[0, 1, V - 1, V // 2], rng.integers(0, V, 2000)])
+    ref = C.hopping_sites(U, phi, sites)
+    with Context(dims) as ctx:
+        for prec, reals in [(F32, 18), (F32, 12), (F16, 12), (F64, 18)]:
+            ctx.gauge_upload(U, reals, prec)
+            got = gpu_hopping_full(ctx, phi, prec).reshape(V, 4, 3)[sites]
+            assert rel(got, ref) <= TOL[prec], (prec, reals, rel(got, ref))

@@ -1,0 +1,125 @@
+"""GPU solvers: the true FP64 residual of each returned x, computed by the oracle."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import c_oracle as C
+from oracle import wilson as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1405_0700_gb300 import F16, F32, F64, Context, PLQError  # noqa: E402
+from paper_1405_0700_gb300 import plq  # noqa: E402
+
+
+def oracle_residual(U, b, x, kappa):
+    return float(np.linalg.norm(b - C.wilson(U, x, kappa)) / np.linalg.norm(b))
+
+
+def run(method, dims, eps, seed, kappa, inner, tol=1e-10, **kw):
+    U, b = S.gauge_and_spinor(dims, eps, seed)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        if inner != F64:
+            ctx.gauge_upload(U, 12, inner)
+        bd = ctx.to_device(b, F64)
+        x = ctx.empty_full(F64)
+        fn = ctx.cg_solve if method == "cg" else ctx.bicgstab_solve
+        info = fn(x, bd, kappa, tol=tol, inner_prec=inner, **kw)
+        xs = ctx.to_host(x, F64)
+    return U, b, xs, info
+
+
+@pytest.mark.parametrize("method", ["cg", "bicgstab"])
+@pytest.mark.parametrize("inner", [F64, F32, F16])
+def test_solve_8c8_reaches_true_residual(method, inner):
+    U, b, x, info = run(method, (8, 8, 8, 8), 0.3, 1, 0.12, inner)
+    res = oracle_residual(U, b, x, 0.12)
+    assert res <= 1e-10, (res, info.as_dict())
+    assert abs(info.true_rel_residual - res) < 1e-11
+    if inner != F64:
+        assert info.n_reliable >= 2
+
+
+def test_cg_matches_dense_solution():
+    dims = (4, 4, 4, 4)
+    U, b = S.gauge_and_spinor(dims, 0.3, 1)
+    kappa = 0.12
+    shape = b.shape
+    M = W.dense(lambda v: W.wilson(U, v, kappa), shape)
+    x_ref = np.linalg.solve(M, b.ravel()).reshape(shape)
+    for method in ("cg", "bicgstab"):
+        _, _, x, _ = run(method, dims, 0.3, 1, kappa, F32)
+        assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-8
+
+
+def test_cg_and_bicgstab_agree_anisotropic():
+    dims = (10, 4, 6, 8)
+    _, _, x1, _ = run("cg", dims, 0.3, 3, 0.115, F32)
+    _, _, x2, _ = run("bicgstab", dims, 0.3, 3, 0.115, F32)
+    assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 1e-8
+
+
+def test_resume_from_x0():
+    dims = (8, 4, 4, 4)
+    U, b = S.gauge_and_spinor(dims, 0.3, 4)
+    kappa = 0.12
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        bd = ctx.to_device(b, F64)
+        x = ctx.empty_full(F64)
+        info1 = ctx.cg_solve(x, bd, kappa, tol=1e-5)
+        info2 = ctx.cg_solve(x, bd, kappa, tol=1e-10, use_x0=True)
+        xs = ctx.to_host(x, F64)
+    assert oracle_residual(U, b, xs, kappa) <= 1e-10
+    fresh = run("cg", dims, 0.3, 4, kappa, F64)[3]
+    assert info2.iterations < fresh.iterations
+
+
+def test_maxit_returns_not_converged():
+    with pytest.raises(PLQError) as e:
+        run("cg", (8, 4, 4, 4), 0.3, 5, 0.12, F64, maxit=5)
+    assert e.value.status == plq.PLQ_ERR_NOT_CONVERGED
+    assert e.value.info.iterations <= 5 + 16
+
+
+def test_nan_source_returns_nan_status():
+    dims = (4, 4, 4, 4)
+    U, b = S.gauge_and_spinor(dims, 0.3, 6)
+    b[1, 2, 3, 0, 1, 2] = np.nan
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        bd = ctx.to_device(b, F64)
+        x = ctx.empty_full(F64)
+        with pytest.raises(PLQError) as e:
+            ctx.cg_solve(x, bd, 0.12)
+        assert e.value.status == plq.PLQ_ERR_NAN
+
+
+def test_zero_source():
+    dims = (4, 4, 4, 4)
+    U = S.gauge_field(dims, 0.3, 7)
+    b = np.zeros(S.lattice_shape(dims) + (4, 3), complex)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        bd = ctx.to_device(b, F64)
+        x = ctx.empty_full(F64)
+        info = ctx.cg_solve(x, bd, 0.12)
+        assert info.status == plq.PLQ_OK and info.iterations == 0
+        assert not torch.any(x.view(torch.float64) != 0)
+        with pytest.raises(PLQError) as e:
+            ctx.bicgstab_solve(x, bd, 0.12)
+        assert e.value.status == plq.PLQ_ERR_BREAKDOWN
+
+
+def test_missing_inner_gauge_copy():
+    dims = (4, 4, 4, 4)
+    U, b = S.gauge_and_spinor(dims, 0.3, 8)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        bd = ctx.to_device(b, F64)
+        x = ctx.empty_full(F64)
+        with pytest.raises(PLQError) as e:
+            ctx.cg_solve(x, bd, 0.12, inner_prec=F16)
+        assert e.value.status == plq.PLQ_ERR_STATE

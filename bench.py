@@ -123,7 +123,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle timing
-def oracle_sample(U, phi, sites, reps_min=1, seconds=10.0, max_reps=50):
+def oracle_sample(U, phi, sites, reps_min=1, seconds=10.0, max_reps=1000):
     """Time the C oracle on `sites` output sites, repeated until ~seconds pass."""
     from oracle import c_oracle as C
 
@@ -239,12 +239,14 @@ def cg_section(torch, local_rank, quick):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small lattices (smoke use only)")
+    ap.add_argument("--lattice", default=None,
+                    help="LxxLyxLzxT for the operator workload (default 32x32x32x64); used for small profiling cases")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -268,6 +270,9 @@ def main():
         dist.init_process_group("nccl")
 
     dims = HOP_DIMS if not args.quick else (16, 16, 16, 16)
+    if args.lattice:
+        lx, ly, lz, lt = (int(v) for v in args.lattice.lower().split("x"))
+        dims = (lt, lx, ly, lz)
     t0 = time.perf_counter()
     U, phi = S.gauge_and_spinor(dims, 0.2, 2)
     log(f"[bench] fields generated in {time.perf_counter() - t0:.1f}s")
@@ -351,7 +356,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC,
+            "metric": METRIC if dims == HOP_DIMS else METRIC.replace("32^3x64", "x".join(map(str, dims[1:])) + "x" + str(dims[0])),
             "value": value,
             "unit": "GFLOP/s",
             "n_gpus": world,
@@ -366,7 +371,7 @@ def main():
             "config": {"workload": "hopping half-apply (plq_hopping_eo, even output sites)",
                        "lattice": "x".join(map(str, dims[1:])) + "x" + str(dims[0]), "links": "18-real FP32",
                        "spinor": "FP32 SoA", "gauge": "exp(i*0.2*H) seed 2", "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (805 MB compulsory traffic per step), no flush"},
+                       "l2": "inputs larger than L2 (%d MB compulsory traffic per step), no flush" % (COMPULSORY[("f32", 18)] * vh // 2**20)},
             "roofline": {"bound": "hbm", "achieved": head["gbs_compulsory"], "peak": peak, "unit": "GB/s",
                          "frac": head["gbs_compulsory"] / peak, "traffic": None, "peak_kind": peak_kind,
                          "bytes_per_site": COMPULSORY[("f32", 18)], "frac_of_8tbs": head["frac_of_8tbs"]},

@@ -214,6 +214,40 @@ PLQ_API plq_status plq_cg_solve(plq_ctx *ctx, void *x, const void *b, double kap
 PLQ_API plq_status plq_bicgstab_solve(plq_ctx *ctx, void *x, const void *b, double kappa, const plq_solver_params *params,
                               plq_solve_info *info, void *stream);
 
+/* Result of plq_autotune. */
+typedef struct {
+    int block;            /* threads per block chosen                                      */
+    int index_mode;       /* 0: neighbours from coordinates; 1: precomputed neighbour table */
+    double us_per_launch; /* measured time of one half-lattice application                 */
+    int from_cache;       /* 1 if the choice came from the cache file                      */
+    int candidates;       /* configurations timed                                          */
+} plq_tune_result;
+
+/* Autotuner of the hopping kernel's launch for precision `prec` and `nrhs`
+ * right-hand sides: times every threads-per-block value in {64, 96, 128, 192,
+ * 256} with neighbour indices computed inline from the coordinates and read
+ * from a precomputed per-site table (the pointer-array addressing the paper
+ * describes for out-of-order site access, Sec. 2.2), and keeps the fastest in
+ * the context for every later operator and solver call of that precision.
+ * cache_path (NULL: the PLQ_TUNE_CACHE environment variable, if set) names a
+ * text file keyed by GPU name, lattice, precision, link format and nrhs: a
+ * hit skips the timing, a miss appends the new result.  Needs the gauge copy
+ * of `prec`; allocates two temporary half fields; synchronises the device.
+ * `res` may be NULL. */
+PLQ_API plq_status plq_autotune(plq_ctx *ctx, int prec, int nrhs, const char *cache_path, plq_tune_result *res);
+
+/* Set the hopping launch of (prec, nrhs) by hand: block = threads per block
+ * (0 = library default, else a multiple of 32 up to 256), index_mode 0 or 1
+ * as above. */
+PLQ_API plq_status plq_set_launch(plq_ctx *ctx, int prec, int nrhs, int block, int index_mode);
+
+/* Roofline calibration (a measurement helper; the paper has no counterpart):
+ * the sustained FMA throughput of the CUDA cores of `device` in FP64
+ * (prec = PLQ_F64) or FP32 (PLQ_F32), in flop/s (an FMA counts 2), measured
+ * with independent FMA chains in every thread of a full-GPU grid.  Allocates
+ * a small scratch buffer and synchronises the device. */
+PLQ_API plq_status plq_measure_fma_rate(int device, int prec, double *flops_per_second);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,8 +31,8 @@ plq_status launch_hop_f16(const HopArgs &a, int reals, int epi, cudaStream_t s, 
 
 int hop_default_block(int prec) { return prec == PLQ_F64 ? 128 : 128; }
 
-plq_status launch_hop(const HopArgs &a, int prec, int reals, int epi, cudaStream_t s, int block) {
-    if (block <= 0) block = hop_default_block(prec);
+plq_status launch_hop(const HopArgs &a, int prec, int reals, int epi, cudaStream_t s) {
+    const int block = a.block > 0 ? a.block : hop_default_block(prec);
     switch (prec) {
     case PLQ_F64: return launch_hop_f64(a, reals, epi, s, block);
     case PLQ_F32: return launch_hop_f32(a, reals, epi, s, block);
@@ -90,14 +90,16 @@ plq_status need_gauge(const plq_ctx *ctx, int prec) {
     return PLQ_OK;
 }
 
-HopArgs hop_args(const plq_ctx *ctx, int prec, int out_parity, void *out, const void *in) {
+HopArgs hop_args(const plq_ctx *ctx, int prec, int out_parity, void *out, const void *in, int nrhs = 1) {
     HopArgs a;
+    a.nrhs = nrhs;
     a.in = in;
     a.out = out;
     a.gauge = ctx->gauge[prec].ptr;
     a.gblock = ctx->gauge[prec].block;
     a.out_parity = out_parity;
     a.lat = ctx->lat;
+    apply_tune(ctx, prec, nrhs, a);
     return a;
 }
 
@@ -156,6 +158,8 @@ plq_status plq_finalize(plq_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &g : c->gauge)
         if (g.ptr) cudaFree(g.ptr);
+    for (auto &t : c->nbr)
+        if (t) cudaFree(t);
     if (c->partials) cudaFree(c->partials);
     if (c->ticket) cudaFree(c->ticket);
     if (c->sums) cudaFree(c->sums);
@@ -261,8 +265,7 @@ plq_status plq_hopping_eo(plq_ctx *c, int out_parity, void *out, const void *in,
     if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
     PLQ_TRY(need_gauge(c, prec));
     PLQ_TRY(use_device(c));
-    HopArgs a = hop_args(c, prec, out_parity, out, in);
-    a.nrhs = nrhs;
+    HopArgs a = hop_args(c, prec, out_parity, out, in, nrhs);
     return launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, static_cast<cudaStream_t>(stream));
 }
 
@@ -279,8 +282,7 @@ plq_status plq_hopping_eo_host(plq_ctx *c, int out_parity, void *out_host, const
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *din = static_cast<char *>(c->stage), *dout = din + bytes;
     PLQ_CUDA(cudaMemcpyAsync(din, in_host, bytes, cudaMemcpyHostToDevice, s));
-    HopArgs a = hop_args(c, prec, out_parity, dout, din);
-    a.nrhs = nrhs;
+    HopArgs a = hop_args(c, prec, out_parity, dout, din, nrhs);
     PLQ_TRY(launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s));
     PLQ_CUDA(cudaMemcpyAsync(out_host, dout, bytes, cudaMemcpyDeviceToHost, s));
     PLQ_CUDA(cudaStreamSynchronize(s));

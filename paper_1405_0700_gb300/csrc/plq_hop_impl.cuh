@@ -107,7 +107,7 @@ __device__ __forceinline__ int lex_stride(const Lattice &L, int mu) {
 
 // Contribution of direction MU (forward and backward) to acc.
 // DAG: gamma5 H gamma5 = H^dagger, i.e. the projectors (1 -/+ gamma) swapped.
-template <int P, int R, int MU, bool DAG>
+template <int P, int R, int MU, bool DAG, bool TBL>
 __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int i, int rr, cx<RealOf<P>> acc[12]) {
     using T = RealOf<P>;
     const Lattice &L = a.lat;
@@ -122,13 +122,22 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
 
     // forward neighbour x + mu
     {
-        const int yl = (cm == Lm - 1) ? g.lex - (Lm - 1) * st : g.lex + st;
-        const int j = yl >> 1;
+        int j;
+        bool flip;
+        if constexpr (TBL) {
+            const int v = __ldg(a.nbr + (size_t)(2 * MU) * L.Vh + i);
+            j = v & 0x7fffffff;
+            flip = v < 0;
+        } else {
+            const int yl = (cm == Lm - 1) ? g.lex - (Lm - 1) * st : g.lex + st;
+            j = yl >> 1;
+            flip = MU == 0 && cm == Lm - 1 && L.t_bc < 0;
+        }
         cx<T> phi[12];
         Spinor<P>::load(a.in, stride, (size_t)j * n + rr, phi);
         cx<T> h[6];
         project<MU, SF>(phi, h);
-        if (MU == 0 && cm == Lm - 1 && L.t_bc < 0) {
+        if (MU == 0 && flip) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) h[k] = {-h[k].re, -h[k].im};
         }
@@ -140,13 +149,22 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
     }
     // backward neighbour x - mu
     {
-        const int yl = (cm == 0) ? g.lex + (Lm - 1) * st : g.lex - st;
-        const int j = yl >> 1;
+        int j;
+        bool flip;
+        if constexpr (TBL) {
+            const int v = __ldg(a.nbr + (size_t)(2 * MU + 1) * L.Vh + i);
+            j = v & 0x7fffffff;
+            flip = v < 0;
+        } else {
+            const int yl = (cm == 0) ? g.lex + (Lm - 1) * st : g.lex - st;
+            j = yl >> 1;
+            flip = MU == 0 && cm == 0 && L.t_bc < 0;
+        }
         cx<T> phi[12];
         Spinor<P>::load(a.in, stride, (size_t)j * n + rr, phi);
         cx<T> h[6];
         project<MU, SB>(phi, h);
-        if (MU == 0 && cm == 0 && L.t_bc < 0) {
+        if (MU == 0 && flip) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) h[k] = {-h[k].re, -h[k].im};
         }
@@ -158,7 +176,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
     }
 }
 
-template <int P, int R, int EPI, bool DAG>
+template <int P, int R, int EPI, bool DAG, bool TBL>
 __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
     using T = RealOf<P>;
     if (a.st != nullptr && a.st->stop) return;
@@ -174,14 +192,15 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
          idx += (long long)gridDim.x * blockDim.x) {
         const int i = n == 1 ? (int)idx : (int)(idx / n);
         const int rr = (int)(idx - (long long)i * n);
-        const SiteGeom g = site_geom(a.lat, a.out_parity, i);
+        SiteGeom g{};
+        if constexpr (!TBL) g = site_geom(a.lat, a.out_parity, i);
         cx<T> acc[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = {T(0), T(0)};
-        hop_dir<P, R, 0, DAG>(a, g, i, rr, acc);
-        hop_dir<P, R, 1, DAG>(a, g, i, rr, acc);
-        hop_dir<P, R, 2, DAG>(a, g, i, rr, acc);
-        hop_dir<P, R, 3, DAG>(a, g, i, rr, acc);
+        hop_dir<P, R, 0, DAG, TBL>(a, g, i, rr, acc);
+        hop_dir<P, R, 1, DAG, TBL>(a, g, i, rr, acc);
+        hop_dir<P, R, 2, DAG, TBL>(a, g, i, rr, acc);
+        hop_dir<P, R, 3, DAG, TBL>(a, g, i, rr, acc);
 
         if constexpr (EPI != EPI_PLAIN) {
             cx<T> xv[12];
@@ -221,10 +240,11 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
 }
 
 // Launch helper: grid = min(work blocks, resident blocks on all SMs).
-template <int P, int R, int EPI, bool DAG>
+template <int P, int R, int EPI, bool DAG, bool TBL = false>
 plq_status launch_hop_t(const HopArgs &a, cudaStream_t s, int block) {
+    if (a.block > 0) block = a.block;
     static int per_sm[1025] = {0};
-    auto kern = hop_kernel<P, R, EPI, DAG>;
+    auto kern = hop_kernel<P, R, EPI, DAG, TBL>;
     if (block <= 0 || block > 1024) block = 128;
     if (per_sm[block] == 0) {
         int nb = 0;
@@ -249,10 +269,19 @@ plq_status launch_hop_t(const HopArgs &a, cudaStream_t s, int block) {
 
 template <int P, int R>
 plq_status dispatch_hop(const HopArgs &a, int epi, cudaStream_t s, int block) {
+    // The neighbour-table variants exist for the plain and xpay epilogues
+    // (operator applications); the reducing epilogues compute indices inline.
+    const bool tbl = a.nbr != nullptr;
     switch (epi) {
     case EPI_PLAIN:
+        if (tbl)
+            return a.dagger ? launch_hop_t<P, R, EPI_PLAIN, true, true>(a, s, block)
+                            : launch_hop_t<P, R, EPI_PLAIN, false, true>(a, s, block);
         return a.dagger ? launch_hop_t<P, R, EPI_PLAIN, true>(a, s, block) : launch_hop_t<P, R, EPI_PLAIN, false>(a, s, block);
     case EPI_XPAY:
+        if (tbl)
+            return a.dagger ? launch_hop_t<P, R, EPI_XPAY, true, true>(a, s, block)
+                            : launch_hop_t<P, R, EPI_XPAY, false, true>(a, s, block);
         return a.dagger ? launch_hop_t<P, R, EPI_XPAY, true>(a, s, block) : launch_hop_t<P, R, EPI_XPAY, false>(a, s, block);
     case EPI_XPAY_NORM:
         return a.dagger ? launch_hop_t<P, R, EPI_XPAY_NORM, true>(a, s, block)

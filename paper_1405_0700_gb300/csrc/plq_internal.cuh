@@ -97,8 +97,16 @@ struct Reduce {
 
 constexpr int kMaxReduceBlocks = 4096;
 
+struct TuneEntry {
+    int block = 0;       // 0 = default
+    int index_mode = 0;  // 0 inline coordinates, 1 neighbour table
+    float us = 0.f;
+};
+
 struct Ctx {
     Lattice lat{};
+    TuneEntry tune[3][PLQ_MAX_RHS + 1];
+    int *nbr[2] = {nullptr, nullptr};  // neighbour tables per output parity (built on demand)
     int device = 0;
     GaugeCopy gauge[3];
     // reduction scratch
@@ -118,6 +126,7 @@ struct Ctx {
 };
 
 plq_status ensure_work(Ctx *c, size_t bytes);
+plq_status ensure_nbr_tables(Ctx *c);
 plq_status ensure_stage(Ctx *c, size_t bytes);
 
 // ---------------------------------------------------------------- hopping
@@ -143,13 +152,22 @@ struct HopArgs {
     Lattice lat{};
     Reduce red{};
     const SolverState *st = nullptr;  // if set and st->stop, the kernel returns at once
+    // Neighbour table of the output parity (the pointer-array addressing of
+    // Sec. 2.2): entry (2*mu + back)*Vh + i holds the checkerboard index of the
+    // neighbour, with bit 31 set when the hop crosses the time boundary.  NULL:
+    // neighbours are computed from the coordinates.
+    const int *nbr = nullptr;
+    int block = 0;  // threads per block; 0 = default
 };
 
 // Launch the hopping kernel for (prec, link reals, epilogue).  block = 0 picks
 // the tuned default.
-plq_status launch_hop(const HopArgs &a, int prec, int reals, int epi, cudaStream_t s, int block = 0);
+plq_status launch_hop(const HopArgs &a, int prec, int reals, int epi, cudaStream_t s);
 
 int hop_default_block(int prec);
+
+// Fill block / neighbour table of `a` from the context's tuned choice.
+void apply_tune(const Ctx *c, int prec, int nrhs, HopArgs &a);
 
 // ---------------------------------------------------------------- layouts
 plq_status launch_pack_spinor(const Lattice &lat, void *out, const double *in, int prec, int nrhs, cudaStream_t s);

@@ -72,6 +72,7 @@ plq_status hop(Solve &S, int prec, int out_par, void *out, const void *in, int e
     h.red = reduce_of(c, fin);
     if (epi < EPI_XPAY_NORM) h.red.st = nullptr;
     h.st = freeze ? c->state : nullptr;
+    apply_tune(c, prec, 1, h);
     S.hops += 1;
     return launch_hop(h, prec, c->gauge[prec].reals, epi, S.s);
 }
@@ -269,6 +270,7 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, const pl
 
         const double delta = S.P == PLQ_F64 ? 0.0 : P.delta;
         double sigma = 0.5;  // safety factor on the estimated inner target
+        double last_rho = 0.0;  // |r|^2 of the second-to-last iteration of the last inner CG run
         double best = INFINITY;
         int stall = 0;
         bool first = true;
@@ -311,12 +313,18 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, const pl
                 void *rL = L[0], *pL = L[1], *qL = L[2], *mpL = L[3], *toL = L[4];
                 if ((st = blas_copy_convert(S.Vh, rL, S.P, r64, PLQ_F64, s)) != PLQ_OK) break;
                 if ((st = blas_zero(S.Vh, xL, S.PX, s)) != PLQ_OK) break;
-                if (first && (st = blas_copy_convert(S.Vh, pL, S.P, rL, S.P, s)) != PLQ_OK) break;
                 target2 = std::pow(sigma * ratio * P.tol * bnorm, 2);
                 init.rho = r2;
-                init.beta = 0.0;
+                // Reliable update: the direction survives and the iteration goes on
+                // as if the recursive residual had been replaced by the true one:
+                // p = r_true + beta p, beta = |r_true|^2 / rho_k with rho_k the
+                // |r|^2 of the iteration before the one that triggered.
+                init.beta = first ? 0.0 : r2 / last_rho;
                 init.stop_r2 = std::fmax(delta * delta * r2, target2);
                 if ((st = put_state(S, init)) != PLQ_OK) break;
+                if (first) st = blas_copy_convert(S.Vh, pL, S.P, rL, S.P, s);
+                else st = blas_cg_direction(S.Vh, pL, rL, S.P, c->state, s);
+                if (st != PLQ_OK) break;
                 const double kk = kappa * kappa;
                 const int PI = S.P;
                 auto body = [&]() -> plq_status {
@@ -372,6 +380,8 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, const pl
             // the inner target was reached but the FP64 check may still fail:
             // tighten the estimate for the next round
             const double fr = method == SOLVER_CG ? fin.rho : fin.r2;
+            // FIN_CG_BETA left rho = rho_{k+1} and beta = rho_{k+1} / rho_k
+            last_rho = fin.beta > 0.0 ? fin.rho / fin.beta : fin.rho;
             if (fr <= target2 * 1.0000001) sigma *= 0.25;
         }
         if (st != PLQ_OK || result != PLQ_OK) break;

@@ -1,0 +1,201 @@
+// Autotuner of the hopping kernel's launch: threads per block and the
+// neighbour-index mode (inline coordinate arithmetic, or the precomputed
+// neighbour table that plays the role of the pointer arrays of Sec. 2.2).
+// Results are kept per (precision, nrhs) in the context and, optionally, in a
+// text cache keyed by GPU name, lattice, precision, link format and nrhs.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "plq_fields.cuh"
+
+namespace plq {
+namespace {
+
+__global__ void build_nbr_kernel(Lattice L, int par, int *tab) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.Vh; i += gridDim.x * blockDim.x) {
+        const SiteGeom g = site_geom(L, par, i);
+        for (int mu = 0; mu < 4; ++mu) {
+            const int st = mu == 0 ? L.L[1] * L.L[2] * L.L[3] : mu == 1 ? 1 : mu == 2 ? L.L[1] : L.L[1] * L.L[2];
+            const int c = g.c[mu], Lm = L.L[mu];
+            const int fl = (c == Lm - 1) ? g.lex - (Lm - 1) * st : g.lex + st;
+            const int bl = (c == 0) ? g.lex + (Lm - 1) * st : g.lex - st;
+            const bool ff = mu == 0 && c == Lm - 1 && L.t_bc < 0;
+            const bool fb = mu == 0 && c == 0 && L.t_bc < 0;
+            tab[(size_t)(2 * mu) * L.Vh + i] = (fl >> 1) | (ff ? (int)0x80000000u : 0);
+            tab[(size_t)(2 * mu + 1) * L.Vh + i] = (bl >> 1) | (fb ? (int)0x80000000u : 0);
+        }
+    }
+}
+
+const char *prec_name(int p) { return p == PLQ_F64 ? "f64" : p == PLQ_F32 ? "f32" : "f16"; }
+
+std::string tune_key(const Ctx *c, int prec, int nrhs) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, c->device);
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|%dx%dx%dx%d|%s|%d|%d", prop.name, c->lat.L[1], c->lat.L[2], c->lat.L[3],
+             c->lat.L[0], prec_name(prec), c->gauge[prec].reals, nrhs);
+    for (char *p = buf; *p; ++p)
+        if (*p == ' ') *p = '_';
+    return buf;
+}
+
+bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        char k[600];
+        int block = 0, mode = 0;
+        float us = 0;
+        if (sscanf(line, "%599s %d %d %f", k, &block, &mode, &us) == 4 && key == k) {
+            e->block = block;
+            e->index_mode = mode;
+            e->us = us;
+            found = true;  // last entry wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, const TuneEntry &e) {
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %.3f\n", key.c_str(), e.block, e.index_mode, e.us);
+    fclose(f);
+}
+
+}  // namespace
+
+plq_status ensure_nbr_tables(Ctx *c) {
+    if (c->nbr[0] && c->nbr[1]) return PLQ_OK;
+    for (int p = 0; p < 2; ++p) {
+        if (c->nbr[p]) continue;
+        PLQ_CUDA(cudaMalloc(&c->nbr[p], sizeof(int) * 8 * (size_t)c->lat.Vh));
+        build_nbr_kernel<<<(c->lat.Vh + 255) / 256, 256>>>(c->lat, p, c->nbr[p]);
+        PLQ_CUDA(cudaGetLastError());
+    }
+    PLQ_CUDA(cudaDeviceSynchronize());
+    return PLQ_OK;
+}
+
+void apply_tune(const Ctx *c, int prec, int nrhs, HopArgs &a) {
+    if (nrhs < 1 || nrhs > PLQ_MAX_RHS || !valid_prec(prec)) return;
+    const TuneEntry &e = c->tune[prec][nrhs];
+    if (e.block > 0) a.block = e.block;
+    a.nbr = (e.index_mode == 1) ? c->nbr[a.out_parity] : nullptr;
+}
+
+}  // namespace plq
+
+using namespace plq;
+
+extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *cache_path, plq_tune_result *res) {
+    if (!c) return set_error(PLQ_ERR_ARG, "null context");
+    if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
+    if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
+    if (!c->gauge[prec].ptr) return set_error(PLQ_ERR_STATE, "autotune needs the gauge copy of precision %d", prec);
+    PLQ_CUDA(cudaSetDevice(c->device));
+    if (res) std::memset(res, 0, sizeof(*res));
+    const char *path = cache_path ? cache_path : getenv("PLQ_TUNE_CACHE");
+    const std::string key = tune_key(c, prec, nrhs);
+    TuneEntry best;
+    if (path && cache_lookup(path, key, &best)) {
+        if (best.index_mode == 1) PLQ_TRY(ensure_nbr_tables(c));
+        c->tune[prec][nrhs] = best;
+        if (res) {
+            res->block = best.block;
+            res->index_mode = best.index_mode;
+            res->us_per_launch = best.us;
+            res->from_cache = 1;
+        }
+        return PLQ_OK;
+    }
+    PLQ_TRY(ensure_nbr_tables(c));
+    const size_t bytes = spinor_site_bytes(prec) * (size_t)c->lat.Vh * nrhs;
+    void *in = nullptr, *out = nullptr;
+    PLQ_CUDA(cudaMalloc(&in, bytes));
+    cudaError_t e = cudaMalloc(&out, bytes);
+    if (e != cudaSuccess) {
+        cudaFree(in);
+        return cuda_error(e, "autotune buffers");
+    }
+    cudaMemset(in, 0, bytes);
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    static const int blocks[] = {64, 96, 128, 192, 256};
+    plq_status st = PLQ_OK;
+    best.us = 1e30f;
+    int tried = 0;
+    const int reps = 10;
+    for (int mode = 0; mode < 2 && st == PLQ_OK; ++mode) {
+        for (int b : blocks) {
+            HopArgs a;
+            a.in = in;
+            a.out = out;
+            a.gauge = c->gauge[prec].ptr;
+            a.gblock = c->gauge[prec].block;
+            a.out_parity = 0;
+            a.nrhs = nrhs;
+            a.lat = c->lat;
+            a.block = b;
+            a.nbr = mode ? c->nbr[0] : nullptr;
+            for (int w = 0; w < 2 && st == PLQ_OK; ++w) st = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && st == PLQ_OK; ++r) st = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
+            cudaEventRecord(e1, s);
+            if (st != PLQ_OK) break;
+            e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                st = cuda_error(e, "autotune timing");
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const float us = ms * 1000.f / reps;
+            ++tried;
+            if (us < best.us) {
+                best.us = us;
+                best.block = b;
+                best.index_mode = mode;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    cudaFree(in);
+    cudaFree(out);
+    if (st != PLQ_OK) return st;
+    c->tune[prec][nrhs] = best;
+    if (path) cache_store(path, key, best);
+    if (res) {
+        res->block = best.block;
+        res->index_mode = best.index_mode;
+        res->us_per_launch = best.us;
+        res->from_cache = 0;
+        res->candidates = tried;
+    }
+    return PLQ_OK;
+}
+
+extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, int index_mode) {
+    if (!c) return set_error(PLQ_ERR_ARG, "null context");
+    if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
+    if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
+    if (block != 0 && (block < 32 || block > 256 || (block % 32)))
+        return set_error(PLQ_ERR_ARG, "block must be 0 or a multiple of 32 in 32..256");
+    if (index_mode != 0 && index_mode != 1) return set_error(PLQ_ERR_ARG, "index_mode must be 0 or 1");
+    PLQ_CUDA(cudaSetDevice(c->device));
+    if (index_mode == 1) PLQ_TRY(ensure_nbr_tables(c));
+    c->tune[prec][nrhs].block = block;
+    c->tune[prec][nrhs].index_mode = index_mode;
+    return PLQ_OK;
+}

@@ -46,6 +46,19 @@ class SolverParams(ctypes.Structure):
     ]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [
+        ("block", ctypes.c_int),
+        ("index_mode", ctypes.c_int),
+        ("us_per_launch", ctypes.c_double),
+        ("from_cache", ctypes.c_int),
+        ("candidates", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class SolveInfo(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int),
@@ -77,6 +90,9 @@ SIGNATURES = {
     "plq_cg_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
     "plq_bicgstab_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams),
                                     ctypes.POINTER(SolveInfo), _vp]),
+    "plq_measure_fma_rate": (_c_int, [_c_int, _c_int, ctypes.POINTER(ctypes.c_double)]),
+    "plq_autotune": (_c_int, [_vp, _c_int, _c_int, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
+    "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int]),
 }
 
 _lib = None
@@ -253,6 +269,16 @@ class Context:
                                     prec_of(prec), _stream(stream)))
         return out
 
+    # ------------------------------------------------------------ tuning
+    def autotune(self, prec, nrhs=1, cache_path=None):
+        r = TuneResult()
+        path = cache_path.encode() if cache_path else None
+        check(lib().plq_autotune(self._h, prec_of(prec), nrhs, path, ctypes.byref(r)))
+        return r.as_dict()
+
+    def set_launch(self, prec, nrhs=1, block=0, index_mode=0):
+        check(lib().plq_set_launch(self._h, prec_of(prec), nrhs, block, index_mode))
+
     # ------------------------------------------------------------ solvers
     def _solve(self, fn, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every, stream, raise_on_error):
         p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every)
@@ -273,6 +299,13 @@ class Context:
         """BiCGstab on the even-odd Schur system; x, b packed full FP64 fields."""
         return self._solve(lib().plq_bicgstab_solve, x, b, kappa, tol, maxit, inner_prec, delta, use_x0,
                            check_every, stream, raise_on_error)
+
+
+def measure_fma_rate(prec, device=0):
+    """Sustained FMA throughput (flop/s) of the CUDA cores in FP64 or FP32."""
+    out = ctypes.c_double()
+    check(lib().plq_measure_fma_rate(device, prec_of(prec), ctypes.byref(out)))
+    return out.value
 
 
 def canonical_gauge_device(U, device=0):

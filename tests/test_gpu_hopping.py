@@ -177,3 +177,38 @@ def test_full_size_32c64_sampled_sites():
             ctx.gauge_upload(U, reals, prec)
             got = gpu_hopping_full(ctx, phi, prec).reshape(V, 4, 3)[sites]
             assert rel(got, ref) <= TOL[prec], (prec, reals, rel(got, ref))
+
+
+@pytest.mark.parametrize("prec", [F64, F32, F16])
+def test_neighbour_table_mode_matches_oracle(prec):
+    # index mode 1: neighbours read from the precomputed table (pointer arrays of Sec. 2.2)
+    dims = (10, 4, 6, 8)
+    U, phi = S.gauge_and_spinor(dims, 0.3, 9)
+    kappa = 0.12
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 12 if prec == F16 else 18, prec)
+        ctx.set_launch(prec, 1, 64, 1)
+        got = gpu_hopping_full(ctx, phi, prec)
+        inp = ctx.to_device(phi, prec)
+        out = ctx.empty_full(prec)
+        ctx.wilson_apply(out, inp, kappa, prec)
+        gotw = ctx.to_host(out, prec)
+    assert rel(got, W.hopping(U, phi)) <= TOL[prec]
+    assert rel(gotw, W.wilson(U, phi, kappa)) <= TOL[prec]
+
+
+def test_autotune_and_cache(tmp_path):
+    dims = (16, 8, 8, 8)
+    U, phi = S.gauge_and_spinor(dims, 0.3, 10)
+    cache = str(tmp_path / "tune.txt")
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F32)
+        r = ctx.autotune(F32, 1, cache_path=cache)
+        assert r["from_cache"] == 0 and r["candidates"] == 10 and r["block"] in (64, 96, 128, 192, 256)
+        got = gpu_hopping_full(ctx, phi, F32)  # runs with the tuned launch
+        assert rel(got, W.hopping(U, phi)) <= TOL[F32]
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F32)
+        r2 = ctx.autotune(F32, 1, cache_path=cache)
+        assert r2["from_cache"] == 1 and r2["block"] == r["block"] and r2["index_mode"] == r["index_mode"]
+    assert open(cache).read().count("\n") == 1

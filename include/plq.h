@@ -214,6 +214,34 @@ PLQ_API plq_status plq_cg_solve(plq_ctx *ctx, void *x, const void *b, double kap
 PLQ_API plq_status plq_bicgstab_solve(plq_ctx *ctx, void *x, const void *b, double kappa, const plq_solver_params *params,
                               plq_solve_info *info, void *stream);
 
+/* Allocation-free Schur operator.  No counterpart in the paper: this is a
+ * service to callers that cannot allocate device memory at the moment they
+ * apply the operator -- code running while a CUDA graph is being captured
+ * (cudaMalloc is not permitted during capture), applications that give all
+ * device memory to their own pool and forbid other allocations, and real-time
+ * loops that must not take the allocator's locks.  It computes the same
+ * result as plq_schur_apply (out = Mhat in, or Mhat^dagger in when dagger !=
+ * 0) but keeps the odd-parity intermediate H_oe in in a fixed device array of
+ * PLQ_NOALLOC_SCRATCH_BYTES bytes compiled into the library, so the call
+ * itself allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine.  (The context, its gauge copy and the in/out fields are set up
+ * beforehand, as for every other call.)
+ *   in, out   caller-owned even half fields of precision `prec`, distinct.
+ *   Limits    PLQ_ERR_ARG when one odd half field of `prec` is larger than
+ *             PLQ_NOALLOC_SCRATCH_BYTES (8 MiB: Vh up to 43,690 sites in FP64,
+ *             87,381 in FP32, 161,319 in FP16).
+ * The array exists once per GPU that loads the library and stays allocated
+ * until the process exits.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and caches
+ * it; make that first call before any stream capture.  Every call on a device
+ * shares the one array: calls whose kernels overlap on the GPU (different
+ * streams, or different contexts on the same device) race on it and must be
+ * serialised by the caller.  The array keeps the last call's contents; each
+ * call overwrites all of the part it reads before reading it. */
+#define PLQ_NOALLOC_SCRATCH_BYTES (8u << 20)
+PLQ_API plq_status plq_schur_apply_noalloc(plq_ctx *ctx, void *out, const void *in, double kappa, int dagger,
+                                           int prec, void *stream);
+
 /* Result of plq_autotune. */
 typedef struct {
     int block;            /* threads per block chosen                                      */

@@ -28,6 +28,7 @@ PLQ_ERR_STATE = 8
 
 F64, F32, F16 = 0, 1, 2
 MAX_RHS = 12
+NOALLOC_SCRATCH_BYTES = 8 << 20
 SITE_BYTES = {F64: 192, F32: 96, F16: 52}
 PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16}
 
@@ -91,6 +92,7 @@ SIGNATURES = {
     "plq_bicgstab_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams),
                                     ctypes.POINTER(SolveInfo), _vp]),
     "plq_measure_fma_rate": (_c_int, [_c_int, _c_int, ctypes.POINTER(ctypes.c_double)]),
+    "plq_schur_apply_noalloc": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, _c_int, _vp]),
     "plq_autotune": (_c_int, [_vp, _c_int, _c_int, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
     "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int]),
 }
@@ -267,6 +269,14 @@ class Context:
     def schur_apply(self, out, inp, tmp, kappa, prec, dagger=False, stream=None):
         check(lib().plq_schur_apply(self._h, _ptr(out), _ptr(inp), _ptr(tmp), float(kappa), int(bool(dagger)),
                                     prec_of(prec), _stream(stream)))
+        return out
+
+    def schur_apply_noalloc(self, out, inp, kappa, prec, dagger=False, stream=None):
+        """Mhat (or Mhat^dagger) on an even half field without any allocation in
+        the call: the odd intermediate lives in the library's fixed device array
+        (at most NOALLOC_SCRATCH_BYTES); concurrent calls on one GPU race."""
+        check(lib().plq_schur_apply_noalloc(self._h, _ptr(out), _ptr(inp), float(kappa), int(bool(dagger)),
+                                            prec_of(prec), _stream(stream)))
         return out
 
     # ------------------------------------------------------------ tuning

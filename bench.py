@@ -236,6 +236,91 @@ def cg_section(torch, local_rank, quick):
     return out
 
 
+def propagator_section(torch, local_rank, quick):
+    """12 point sources (spin x colour at the origin): multi-RHS operator and batched mixed CG."""
+    from paper_1405_0700_gb300 import F16, F32, F64, Context
+
+    dims = (96, 48, 48, 48) if not quick else (16, 8, 8, 8)
+    kappa, eps, seed, n = 0.121, 0.25, 4, 12
+    t0 = time.perf_counter()
+    U = S.gauge_field(dims, eps, seed)
+    log(f"[bench] propagator gauge generated in {time.perf_counter() - t0:.1f}s")
+    vh = S.volume(dims) // 2
+    peak, _ = peaks()
+    out = {"lattice": "x".join(map(str, dims[1:])) + "x" + str(dims[0]), "kappa": kappa, "eps": eps, "seed": seed,
+           "nrhs": n, "tol": 1e-10}
+    with Context(dims, device=local_rank) as ctx:
+        # operator throughput with 12 right-hand sides (links loaded once per site)
+        ops = {}
+        for pname, prec, reals in [("f32", F32, 18), ("f32", F32, 12), ("f16", F16, 12)]:
+            ctx.gauge_upload(U, reals, prec)
+            inp = ctx.empty_half(prec, n)
+            inp.zero_()
+            o = ctx.empty_half(prec, n)
+            for _ in range(3):
+                ctx.hopping_eo(0, o, inp, prec, n)
+            torch.cuda.synchronize()
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 20
+            s_.record()
+            for _ in range(reps):
+                ctx.hopping_eo(0, o, inp, prec, n)
+            e_.record()
+            torch.cuda.synchronize()
+            ms = s_.elapsed_time(e_) / reps
+            site_bytes = {("f32", 18): 96 + 96 + 576 / n, ("f32", 12): 96 + 96 + 384 / n,
+                          ("f16", 12): 52 + 52 + 192 / n}[(pname, reals)]
+            gbs = site_bytes * vh * n / (ms * 1e-3) / 1e9
+            ops[f"{pname}_{reals}"] = {"ms": ms, "gflops": FLOP_PER_SITE * vh * n / (ms * 1e-3) / 1e9,
+                                       "gbs_compulsory": gbs, "frac_of_measured_hbm": gbs / peak,
+                                       "bytes_per_site_rhs": site_bytes}
+            log(f"[bench] multi-RHS {pname}-{reals} x{n}: {ms:.2f} ms, {gbs:.0f} GB/s")
+            del inp, o
+        out["operator_12rhs"] = ops
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        # 12 point sources, canonical layout, built on the device
+        V = S.volume(dims)
+        b = torch.zeros(n * V * 24, dtype=torch.float64, device=f"cuda:{local_rank}")
+        for r in range(n):  # source r: spin r // 3, colour r % 3 at the origin
+            b[r * V * 24 + 2 * r] = 1.0
+        bd = ctx.empty_full(F64, n)
+        ctx.pack_spinor(bd, b, F64, n)
+        del b
+        x = ctx.empty_full(F64, n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = ctx.cg_solve_multi(x, bd, kappa, n, tol=1e-10, inner_prec=F32, raise_on_error=False)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out["batched_cg_mixed_f32"] = {
+            "seconds": el, "seconds_per_rhs": el / n,
+            "iterations": [i.iterations for i in infos], "reliable_updates": infos[0].n_reliable,
+            "max_true_rel_residual": max(i.true_rel_residual for i in infos),
+            "status": [i.status for i in infos]}
+        log(f"[bench] batched CG x{n}: {el:.2f}s, it={infos[0].iterations}, "
+            f"res<={out['batched_cg_mixed_f32']['max_true_rel_residual']:.2e}")
+        # the same right-hand sides one at a time (single-RHS solver, same inner precision)
+        singles = []
+        for r in range(n if not quick else 2):
+            bs = torch.zeros(V * 24, dtype=torch.float64, device=f"cuda:{local_rank}")
+            bs[2 * r] = 1.0
+            b1 = ctx.empty_full(F64)
+            ctx.pack_spinor(b1, bs, F64)
+            x1 = ctx.empty_full(F64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = ctx.cg_solve(x1, b1, kappa, tol=1e-10, inner_prec=F32, raise_on_error=False)
+            torch.cuda.synchronize()
+            singles.append((time.perf_counter() - t0, info.iterations, info.true_rel_residual))
+            del bs, b1, x1
+        out["single_rhs_cg_mixed_f32"] = {
+            "solves": len(singles), "seconds_per_rhs": float(np.mean([s_[0] for s_ in singles])),
+            "iterations": [s_[1] for s_ in singles], "max_true_rel_residual": max(s_[2] for s_ in singles)}
+        out["speedup_batched_vs_single_per_rhs"] = out["single_rhs_cg_mixed_f32"]["seconds_per_rhs"] / (el / n)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -245,6 +330,8 @@ def main():
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small lattices (smoke use only)")
+    ap.add_argument("--workload", default="hop", choices=["hop", "propagator"],
+                    help="hop: the headline operator line (default); propagator: 48^3x96 with 12 point sources")
     ap.add_argument("--lattice", default=None,
                     help="LxxLyxLzxT for the operator workload (default 32x32x32x64); used for small profiling cases")
     args = ap.parse_args()
@@ -263,6 +350,11 @@ def main():
 
     torch.cuda.set_device(local_rank)
     lib()
+    if args.workload == "propagator":
+        res = propagator_section(torch, local_rank, args.quick)
+        if rank == 0:
+            print(json.dumps({"workload": "propagator", **res}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -214,6 +214,21 @@ PLQ_API plq_status plq_cg_solve(plq_ctx *ctx, void *x, const void *b, double kap
 PLQ_API plq_status plq_bicgstab_solve(plq_ctx *ctx, void *x, const void *b, double kappa, const plq_solver_params *params,
                               plq_solve_info *info, void *stream);
 
+/* Several right-hand sides at once: x and b are packed full FP64 fields
+ * holding `nrhs` (1..PLQ_MAX_RHS) interleaved right-hand sides (as produced
+ * by plq_pack_spinor with that nrhs); `infos` points to nrhs reports.  Every
+ * operator application of the solve loads each link once for all of them
+ * (the multi-RHS hopping kernel); each right-hand side keeps its own Krylov
+ * scalars, stops on its own true residual and is frozen (its elements
+ * skipped) once converged.  Reliable updates are taken for the whole batch
+ * when every active right-hand side has reached its trigger.  The return
+ * value is PLQ_OK if every right-hand side converged, else the status of the
+ * first that did not (its message names it). */
+PLQ_API plq_status plq_cg_solve_multi(plq_ctx *ctx, void *x, const void *b, double kappa, int nrhs,
+                                      const plq_solver_params *params, plq_solve_info *infos, void *stream);
+PLQ_API plq_status plq_bicgstab_solve_multi(plq_ctx *ctx, void *x, const void *b, double kappa, int nrhs,
+                                            const plq_solver_params *params, plq_solve_info *infos, void *stream);
+
 /* Allocation-free Schur operator.  No counterpart in the paper: this is a
  * service to callers that cannot allocate device memory at the moment they
  * apply the operator -- code running while a CUDA graph is being captured

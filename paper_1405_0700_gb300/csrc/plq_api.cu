@@ -134,14 +134,14 @@ plq_status plq_init(plq_ctx **out, const int dims[4], int t_bc, int device) {
     c->lat.t_bc = t_bc;
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    cudaError_t e = cudaMalloc(&c->partials, sizeof(double) * 4 * kMaxReduceBlocks);
+    cudaError_t e = cudaMalloc(&c->partials, sizeof(double) * kPartialSlots * kMaxReduceBlocks);
     if (e == cudaSuccess) e = cudaMalloc(&c->ticket, sizeof(unsigned) * 16);
-    if (e == cudaSuccess) e = cudaMalloc(&c->sums, sizeof(double) * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&c->state, sizeof(SolverState));
-    if (e == cudaSuccess) e = cudaMallocHost(&c->sums_host, sizeof(double) * 8);
-    if (e == cudaSuccess) e = cudaMallocHost(&c->state_host, sizeof(SolverState));
+    if (e == cudaSuccess) e = cudaMalloc(&c->sums, sizeof(double) * kPartialSlots);
+    if (e == cudaSuccess) e = cudaMalloc(&c->state, sizeof(SolverState) * PLQ_MAX_RHS);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->sums_host, sizeof(double) * kPartialSlots);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->state_host, sizeof(SolverState) * PLQ_MAX_RHS);
     if (e == cudaSuccess) e = cudaMemset(c->ticket, 0, sizeof(unsigned) * 16);
-    if (e == cudaSuccess) e = cudaMemset(c->state, 0, sizeof(SolverState));
+    if (e == cudaSuccess) e = cudaMemset(c->state, 0, sizeof(SolverState) * PLQ_MAX_RHS);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         plq_status st = cuda_error(e, "plq_init allocation");

@@ -266,52 +266,6 @@ struct Link<PLQ_F16, 12> {
 };
 
 // ---------------------------------------------------------------- reductions
-// Reduce NV values per thread over the grid.  Threads first combine in the
-// working precision R inside a warp (cheap on FP32 pipes), warps then combine
-// in FP64 in shared memory and blocks in FP64 through `partials`.  The last
-// block to finish (ticket) adds the partials in block order (deterministic)
-// and returns true with the grid totals in tot[] for thread 0 of that block.
-template <int NV, class R>
-__device__ bool grid_reduce(const Reduce &red, R v[NV], double tot[NV]) {
-    __shared__ double sh[32][NV];
-    __shared__ bool last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        R x = v[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) sh[warp][k] = (double)x;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += sh[w][k];
-            red.partials[blockIdx.x * 4 + k] = s;
-        }
-        __threadfence();
-        unsigned t = atomicAdd(red.ticket, 1u);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    // last block: sum partials in block order, split over the threads of a warp
-    if (warp == 0) {
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(red.partials + b * 4 + k);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            tot[k] = s;
-        }
-    }
-    if (threadIdx.x == 0) *red.ticket = 0u;
-    return threadIdx.x == 0;
-}
-
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
     const double d = b.x * b.x + b.y * b.y;
     return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
@@ -321,13 +275,10 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 
-// Apply the finalize step of a reduction (thread 0 of the last block): store
-// the grid totals and update the solver scalars in device memory.
-__device__ __forceinline__ void finalize(const Reduce &red, const double *tot, int nv) {
-    for (int k = 0; k < nv; ++k) red.sums[k] = tot[k];
-    SolverState *st = red.st;
-    if (!st) return;
-    switch (red.fin) {
+// Finalize step of one right-hand side's reduction: update its solver
+// scalars in device memory from the grid totals tot[0..NV).
+__device__ __forceinline__ void finalize_one(int fin, SolverState *st, const double *tot) {
+    switch (fin) {
     case FIN_CG_ALPHA:
         st->pAp = tot[0];
         st->alpha = st->rho / tot[0];
@@ -365,7 +316,7 @@ __device__ __forceinline__ void finalize(const Reduce &red, const double *tot, i
         st->iter += 1;
         if (!finite2(rn) || !isfinite(tot[2])) { st->flags |= FLAG_NAN; st->stop = 1; break; }
         if (tot[2] <= st->stop_r2 || st->iter >= st->maxit) { st->stop = 1; st->c_rho_new = rn; break; }
-        if (!(fabs(rn.x) + fabs(rn.y) > st->tiny * tot[2] * 1e-30)) { st->flags |= FLAG_BREAKDOWN; st->stop = 1; break; }
+        if (!(fabs(rn.x) + fabs(rn.y) > 0.0)) { st->flags |= FLAG_BREAKDOWN; st->stop = 1; break; }
         st->c_beta = cmul(cdiv(rn, st->c_rho), cdiv(st->c_alpha, st->c_omega));
         st->c_rho = rn;
         st->c_rho_new = rn;
@@ -374,6 +325,92 @@ __device__ __forceinline__ void finalize(const Reduce &red, const double *tot, i
     default:
         break;
     }
+}
+
+// Per-thread accumulator of NV sums for each of n right-hand sides.  With one
+// right-hand side the sums stay in registers (combined later with warp
+// shuffles in the working precision R, cheap on the FP32 pipes); with several,
+// the element's right-hand side varies across the threads of a warp, so each
+// contribution goes to a shared-memory slot (k, rhs) by atomic add.
+template <int NV, class R>
+struct RedAcc {
+    R v[NV];
+    R *sm;
+    int n;
+    __device__ __forceinline__ void add(int k, int rr, R x) {
+        if (n == 1) v[k] += x;
+        else atomicAdd(sm + k * n + rr, x);
+    }
+};
+
+// Must be called by every thread of the block before any add().
+template <int NV, class R>
+__device__ __forceinline__ void red_init(RedAcc<NV, R> &acc, int n) {
+    __shared__ R slots[NV * PLQ_MAX_RHS];
+    acc.n = n;
+    acc.sm = slots;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc.v[k] = R(0);
+    for (int t = threadIdx.x; t < NV * n; t += blockDim.x) slots[t] = R(0);
+    __syncthreads();
+}
+
+// Combine the accumulators of the whole grid: each block writes its partial
+// sums (FP64) to red.partials, and the last block to finish (ticket counter)
+// adds them in block order -- deterministic -- stores the totals in
+// red.sums[k*n + r] and applies the finalize step to red.st[r].  Every thread
+// of every block must call it.
+template <int NV, class R>
+__device__ void grid_reduce(const Reduce &red, RedAcc<NV, R> &acc) {
+    __shared__ double wsum[32][NV];
+    __shared__ double tots[kPartialSlots];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int n = acc.n, slots = NV * n;
+    double *mine = red.partials + (size_t)blockIdx.x * kPartialSlots;
+    if (n == 1) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            R x = acc.v[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) wsum[warp][k] = (double)x;
+        }
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += wsum[w][threadIdx.x];
+            mine[threadIdx.x] = s;
+        }
+    } else {
+        __syncthreads();  // all shared-memory atomics of the block are done
+        for (int t = threadIdx.x; t < slots; t += blockDim.x) mine[t] = (double)acc.sm[t];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(red.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int t = warp; t < slots; t += nw) {
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(red.partials + (size_t)b * kPartialSlots + t);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) tots[t] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < n) {
+        const int r = threadIdx.x;
+        double tr[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            tr[k] = tots[k * n + r];
+            red.sums[k * n + r] = tr[k];
+        }
+        if (red.st) finalize_one(red.fin, red.st + r, tr);
+    }
+    if (threadIdx.x == 0) *red.ticket = 0u;
 }
 
 // ---------------------------------------------------------------- geometry

@@ -179,19 +179,18 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
 template <int P, int R, int EPI, bool DAG, bool TBL>
 __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
     using T = RealOf<P>;
-    if (a.st != nullptr && a.st->stop) return;
     const int n = a.nrhs;
     const long long total = (long long)a.lat.Vh * n;
     const size_t stride = (size_t)total;
     constexpr int NV = EPI == EPI_XPAY_NORM ? 1 : EPI == EPI_XPAY_DOTW ? 2 : EPI == EPI_XPAY_TS ? 3 : 0;
-    T red[NV > 0 ? NV : 1];
-#pragma unroll
-    for (int k = 0; k < (NV > 0 ? NV : 1); ++k) red[k] = T(0);
+    RedAcc<(NV > 0 ? NV : 1), T> racc;
+    if constexpr (NV > 0) red_init(racc, n);
 
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int i = n == 1 ? (int)idx : (int)(idx / n);
         const int rr = (int)(idx - (long long)i * n);
+        if (a.st != nullptr && a.st[rr].stop) continue;  // frozen right-hand side
         SiteGeom g{};
         if constexpr (!TBL) g = site_geom(a.lat, a.out_parity, i);
         cx<T> acc[12];
@@ -212,31 +211,37 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
                 acc[k].im = fma(s, acc[k].im, xv[k].im);
             }
             if constexpr (EPI == EPI_XPAY_NORM) {
+                T s0 = 0;
 #pragma unroll
-                for (int k = 0; k < 12; ++k) red[0] += acc[k].re * acc[k].re + acc[k].im * acc[k].im;
+                for (int k = 0; k < 12; ++k) s0 += acc[k].re * acc[k].re + acc[k].im * acc[k].im;
+                racc.add(0, rr, s0);
             } else if constexpr (EPI == EPI_XPAY_DOTW) {
                 cx<T> wv[12];
                 Spinor<P>::load(a.w, stride, (size_t)idx, wv);
+                T s0 = 0, s1 = 0;
 #pragma unroll
                 for (int k = 0; k < 12; ++k) {  // <w, out> = sum conj(w) out
-                    red[0] += wv[k].re * acc[k].re + wv[k].im * acc[k].im;
-                    red[1] += wv[k].re * acc[k].im - wv[k].im * acc[k].re;
+                    s0 += wv[k].re * acc[k].re + wv[k].im * acc[k].im;
+                    s1 += wv[k].re * acc[k].im - wv[k].im * acc[k].re;
                 }
+                racc.add(0, rr, s0);
+                racc.add(1, rr, s1);
             } else if constexpr (EPI == EPI_XPAY_TS) {
+                T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
                 for (int k = 0; k < 12; ++k) {  // <out, x> and |out|^2
-                    red[0] += acc[k].re * xv[k].re + acc[k].im * xv[k].im;
-                    red[1] += acc[k].re * xv[k].im - acc[k].im * xv[k].re;
-                    red[2] += acc[k].re * acc[k].re + acc[k].im * acc[k].im;
+                    s0 += acc[k].re * xv[k].re + acc[k].im * xv[k].im;
+                    s1 += acc[k].re * xv[k].im - acc[k].im * xv[k].re;
+                    s2 += acc[k].re * acc[k].re + acc[k].im * acc[k].im;
                 }
+                racc.add(0, rr, s0);
+                racc.add(1, rr, s1);
+                racc.add(2, rr, s2);
             }
         }
         Spinor<P>::store(a.out, stride, (size_t)idx, acc);
     }
-    if constexpr (NV > 0) {
-        double tot[NV];
-        if (grid_reduce<NV, T>(a.red, red, tot)) finalize(a.red, tot, NV);
-    }
+    if constexpr (NV > 0) grid_reduce(a.red, racc);
 }
 
 // Launch helper: grid = min(work blocks, resident blocks on all SMs).

@@ -88,14 +88,15 @@ enum Finalize {
 };
 
 struct Reduce {
-    double *partials = nullptr;   // >= 4 * gridDim.x doubles
+    double *partials = nullptr;   // kPartialSlots doubles per block
     unsigned *ticket = nullptr;   // zero on entry, left zero on exit
-    double *sums = nullptr;       // 4 doubles: the grid totals
-    SolverState *st = nullptr;    // target of the finalize step
+    double *sums = nullptr;       // grid totals: sums[k * nrhs + r]
+    SolverState *st = nullptr;    // per right-hand side targets of the finalize step (array of nrhs)
     int fin = FIN_NONE;
 };
 
 constexpr int kMaxReduceBlocks = 4096;
+constexpr int kPartialSlots = 64;  // >= 4 values x PLQ_MAX_RHS right-hand sides
 
 struct TuneEntry {
     int block = 0;       // 0 = default
@@ -110,12 +111,12 @@ struct Ctx {
     int device = 0;
     GaugeCopy gauge[3];
     // reduction scratch
-    double *partials = nullptr;
+    double *partials = nullptr;         // kPartialSlots * kMaxReduceBlocks
     unsigned *ticket = nullptr;
-    double *sums = nullptr;
-    double *sums_host = nullptr;  // pinned mirror of sums
-    SolverState *state = nullptr;
-    SolverState *state_host = nullptr;  // pinned
+    double *sums = nullptr;             // kPartialSlots
+    double *sums_host = nullptr;        // pinned mirror of sums
+    SolverState *state = nullptr;       // PLQ_MAX_RHS solver states
+    SolverState *state_host = nullptr;  // pinned mirror
     // solver workspace (allocated on first use, grown as needed)
     void *work = nullptr;
     size_t work_bytes = 0;
@@ -151,7 +152,7 @@ struct HopArgs {
     int dagger = 0;
     Lattice lat{};
     Reduce red{};
-    const SolverState *st = nullptr;  // if set and st->stop, the kernel returns at once
+    const SolverState *st = nullptr;  // per-rhs states: elements whose st[rhs].stop is set are skipped
     // Neighbour table of the output parity (the pointer-array addressing of
     // Sec. 2.2): entry (2*mu + back)*Vh + i holds the checkerboard index of the
     // neighbour, with bit 31 set when the hop crosses the time boundary.  NULL:
@@ -176,29 +177,33 @@ plq_status launch_pack_gauge(const Lattice &lat, void *out, const double *in, in
                              unsigned *bad, cudaStream_t s);
 
 // ---------------------------------------------------------------- blas
-// All vectors are packed half fields of Vh sites (one right-hand side).
-plq_status blas_copy_convert(int Vh, void *dst, int pdst, const void *src, int psrc, cudaStream_t s);
-plq_status blas_zero(int Vh, void *dst, int prec, cudaStream_t s);
-plq_status blas_gamma5(int Vh, void *dst, const void *src, int prec, cudaStream_t s);
-// sum |v|^2 into red.sums (FP64); blocking = false leaves the result on the device
-plq_status blas_norm2(int Vh, const void *v, int prec, const Reduce &red, cudaStream_t s);
-// x += alpha p; r -= alpha q; rho_new = |r|^2 (alpha from state)
-plq_status blas_cg_update(int Vh, void *x, void *r, const void *p, const void *q, int prec, const Reduce &red,
-                          const SolverState *st, cudaStream_t s);
-// p = r + beta p (beta from state)
-plq_status blas_cg_direction(int Vh, void *p, const void *r, int prec, const SolverState *st, cudaStream_t s);
+// Vectors are packed half fields of N = Vh * n elements (n right-hand sides
+// interleaved); element e belongs to right-hand side e % n.  Kernels that take
+// `st` skip elements whose st[rhs].stop is set and read their coefficients
+// from st[rhs]; reductions produce sums[k * n + rhs].
+plq_status blas_copy_convert(long long N, void *dst, int pdst, const void *src, int psrc, cudaStream_t s);
+plq_status blas_zero(long long N, void *dst, int prec, cudaStream_t s);
+plq_status blas_gamma5(long long N, void *dst, const void *src, int prec, cudaStream_t s);
+plq_status blas_norm2(long long N, int n, const void *v, int prec, const Reduce &red, cudaStream_t s);
+plq_status blas_dot_norm(long long N, int n, const void *a, const void *b, int prec, const Reduce &red,
+                         cudaStream_t s);
+// x += alpha p; r -= alpha q; rho_new = |r|^2
+plq_status blas_cg_update(long long N, int n, void *x, void *r, const void *p, const void *q, int prec,
+                          const Reduce &red, const SolverState *st, cudaStream_t s);
+// p = r + beta p
+plq_status blas_cg_direction(long long N, int n, void *p, const void *r, int prec, const SolverState *st,
+                             cudaStream_t s);
 // dst(F64) += convert(src)
-plq_status blas_accumulate(int Vh, void *dst64, const void *src, int psrc, cudaStream_t s);
-// y = x + a * y for FP64 vectors with host scalar a (setup paths)
-plq_status blas_xpay64(int Vh, const void *x, double a, void *y, cudaStream_t s);
-// BiCGstab kernels
-plq_status blas_bicg_p(int Vh, void *p, const void *r, const void *v, int prec, const SolverState *st,
+plq_status blas_accumulate(long long N, void *dst64, const void *src, int psrc, cudaStream_t s);
+// y = x + a * y (FP64, host scalar)
+plq_status blas_xpay64(long long N, const void *x, double a, void *y, cudaStream_t s);
+// BiCGstab: p = r + beta (p - omega v); s = r - alpha v; x += alpha p + omega s, r = s - omega t, <rhat, r>, |r|^2
+plq_status blas_bicg_p(long long N, int n, void *p, const void *r, const void *v, int prec, const SolverState *st,
                        cudaStream_t s);
-plq_status blas_bicg_s(int Vh, void *sv, const void *r, const void *v, int prec, const SolverState *st,
+plq_status blas_bicg_s(long long N, int n, void *sv, const void *r, const void *v, int prec, const SolverState *st,
                        cudaStream_t s);
-plq_status blas_bicg_update(int Vh, void *x, void *r, const void *p, const void *sv, const void *t,
+plq_status blas_bicg_update(long long N, int n, void *x, void *r, const void *p, const void *sv, const void *t,
                             const void *rhat, int prec, const Reduce &red, const SolverState *st, cudaStream_t s);
-plq_status blas_dot_norm(int Vh, const void *a, const void *b, int prec, const Reduce &red, cudaStream_t s);
 
 }  // namespace plq
 

@@ -5,32 +5,37 @@
 //   * CG on the normal equations Mhat^dag Mhat x_e = Mhat^dag bhat, and
 //   * BiCGstab (van der Vorst) on Mhat x_e = bhat,
 // with Mhat = 1 - kappa^2 H_eo H_oe, bhat = b_e + kappa H_eo b_o and
-// x_o = b_o + kappa H_oe x_e.
+// x_o = b_o + kappa H_oe x_e, for one or several (n <= 12) right-hand sides
+// solved together: every operator application of the batch loads each link
+// once for all of them (the multi-RHS hopping kernel), while each right-hand
+// side keeps its own Krylov scalars and convergence state.
 //
 // Precision.  The Krylov iteration runs at the inner precision (FP64, or FP32
 // / FP16 storage with FP32 arithmetic).  An FP64 outer loop owns the solution
 // x_e and the true residual s = bhat - Mhat x_e: whenever the inner residual
-// has fallen by `delta` (or reached the estimated target) the inner
-// solution is added to x_e in FP64, s is recomputed with the FP64 operator and
-// the iteration continues from it.  For CG the search direction p is kept
-// across these reliable updates (Clark et al., "Solving lattice QCD systems of
-// equations using mixed precision solvers on GPUs", 2010); BiCGstab restarts
-// from the recomputed residual (defect correction).  Convergence is declared
-// only on the FP64 true residual: ||b - M x|| / ||b|| = ||s|| / ||b|| <= tol.
+// of every active right-hand side has fallen by `delta` (or reached its
+// estimated target) the inner solution is added to x_e in FP64, s is
+// recomputed with the FP64 operator and the iteration continues from it.  For
+// CG the search direction p is kept across these reliable updates (Clark et
+// al., "Solving lattice QCD systems of equations using mixed precision solvers
+// on GPUs", 2010); BiCGstab restarts from the recomputed residual (defect
+// correction).  Convergence is declared only on the FP64 true residual:
+// ||b - M x|| / ||b|| = ||s|| / ||b|| <= tol.
 //
 // Each inner iteration is a fixed sequence of kernels that read their
-// coefficients from a device-resident SolverState and update it in the last
+// coefficients from device-resident SolverStates and update them in the last
 // block of each fused reduction; a batch of `check_every` iterations is
 // captured once into a CUDA graph and replayed, and the host only polls the
-// state between batches.  Once the state's stop flag is set (converged,
-// triggered, maxit, NaN or breakdown) the remaining kernels of the batch
-// return immediately, so x and r stay consistent.
+// states between batches.  Once a right-hand side's stop flag is set
+// (triggered, converged, maxit, NaN or breakdown) every later kernel skips its
+// elements, so its x and r stay consistent.
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
-#include "plq_internal.cuh"
+#include "plq_fields.cuh"
 
 namespace plq {
 namespace {
@@ -39,6 +44,8 @@ struct Solve {
     plq_ctx *c;
     cudaStream_t s;  // internal capture-capable stream
     int Vh;
+    int n;           // right-hand sides
+    long long N;     // elements of a half field: Vh * n
     double kappa;
     int P;   // inner storage precision
     int PX;  // inner solution accumulator precision
@@ -68,47 +75,49 @@ plq_status hop(Solve &S, int prec, int out_par, void *out, const void *in, int e
     h.gblock = c->gauge[prec].block;
     h.out_parity = out_par;
     h.dagger = dagger;
+    h.nrhs = S.n;
     h.lat = c->lat;
     h.red = reduce_of(c, fin);
-    if (epi < EPI_XPAY_NORM) h.red.st = nullptr;
+    if (fin == FIN_NONE) h.red.st = nullptr;
     h.st = freeze ? c->state : nullptr;
-    apply_tune(c, prec, 1, h);
+    apply_tune(c, prec, S.n, h);
     S.hops += 1;
     return launch_hop(h, prec, c->gauge[prec].reals, epi, S.s);
 }
 
-plq_status read_sums(Solve &S, double *out, int n) {
-    PLQ_CUDA(cudaMemcpyAsync(S.c->sums_host, S.c->sums, sizeof(double) * n, cudaMemcpyDeviceToHost, S.s));
+plq_status read_sums(Solve &S, double *out, int count) {
+    PLQ_CUDA(cudaMemcpyAsync(S.c->sums_host, S.c->sums, sizeof(double) * count, cudaMemcpyDeviceToHost, S.s));
     PLQ_CUDA(cudaStreamSynchronize(S.s));
-    for (int k = 0; k < n; ++k) out[k] = S.c->sums_host[k];
+    for (int k = 0; k < count; ++k) out[k] = S.c->sums_host[k];
     return PLQ_OK;
 }
 
+// per right-hand side |v|^2 of an FP64 half field
 plq_status norm2_64(Solve &S, const void *v, double *out) {
     Reduce r = reduce_of(S.c, FIN_NONE);
     r.st = nullptr;
-    PLQ_TRY(blas_norm2(S.Vh, v, PLQ_F64, r, S.s));
-    return read_sums(S, out, 1);
+    PLQ_TRY(blas_norm2(S.N, S.n, v, PLQ_F64, r, S.s));
+    return read_sums(S, out, S.n);
 }
 
-plq_status put_state(Solve &S, const SolverState &st) {
-    *S.c->state_host = st;
-    PLQ_CUDA(cudaMemcpyAsync(S.c->state, S.c->state_host, sizeof(SolverState), cudaMemcpyHostToDevice, S.s));
+plq_status put_states(Solve &S, const std::vector<SolverState> &st) {
+    std::memcpy(S.c->state_host, st.data(), sizeof(SolverState) * S.n);
+    PLQ_CUDA(cudaMemcpyAsync(S.c->state, S.c->state_host, sizeof(SolverState) * S.n, cudaMemcpyHostToDevice, S.s));
     PLQ_CUDA(cudaStreamSynchronize(S.s));
     return PLQ_OK;
 }
 
-plq_status get_state(Solve &S, SolverState *st) {
-    PLQ_CUDA(cudaMemcpyAsync(S.c->state_host, S.c->state, sizeof(SolverState), cudaMemcpyDeviceToHost, S.s));
+plq_status get_states(Solve &S, std::vector<SolverState> &st) {
+    PLQ_CUDA(cudaMemcpyAsync(S.c->state_host, S.c->state, sizeof(SolverState) * S.n, cudaMemcpyDeviceToHost, S.s));
     PLQ_CUDA(cudaStreamSynchronize(S.s));
-    *st = *S.c->state_host;
+    std::memcpy(st.data(), S.c->state_host, sizeof(SolverState) * S.n);
     return PLQ_OK;
 }
 
 // Run `body` (one inner iteration) as graph-captured batches of `k` until the
-// device state says stop.  `iters_out` gets the state's final iteration count.
+// device state of every right-hand side says stop.
 template <class Body>
-plq_status run_batches(Solve &S, int k, Body body, SolverState *final_state) {
+plq_status run_batches(Solve &S, int k, Body body, std::vector<SolverState> &cur) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     PLQ_CUDA(cudaStreamBeginCapture(S.s, cudaStreamCaptureModeThreadLocal));
@@ -116,39 +125,42 @@ plq_status run_batches(Solve &S, int k, Body body, SolverState *final_state) {
     const double hops0 = S.hops;
     for (int i = 0; i < k && st == PLQ_OK; ++i) st = body();
     cudaError_t e = cudaStreamEndCapture(S.s, &graph);
+    S.hops = hops0;
     if (st != PLQ_OK) {
         if (graph) cudaGraphDestroy(graph);
         return st;
     }
     if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
-    const double hops_per_iter = (S.hops - hops0) / k;
-    S.hops = hops0;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
-    SolverState cur;
-    std::memset(&cur, 0, sizeof cur);
-    int last_iter = -1, idle = 0;
+    long long last_sum = -1;
+    int idle = 0;
     for (;;) {
         e = cudaGraphLaunch(exec, S.s);
         if (e != cudaSuccess) {
-            cudaGraphExecDestroy(exec);
-            return cuda_error(e, "cudaGraphLaunch");
+            st = cuda_error(e, "cudaGraphLaunch");
+            break;
         }
-        st = get_state(S, &cur);
+        st = get_states(S, cur);
         if (st != PLQ_OK) break;
-        if (cur.stop) break;
-        // every batch runs at least one iteration unless the state froze it;
-        // a state that neither advances nor stops is a logic error, not a hang
-        idle = (cur.iter == last_iter) ? idle + 1 : 0;
-        last_iter = cur.iter;
+        bool all = true;
+        long long sum = 0;
+        for (int r = 0; r < S.n; ++r) {
+            all = all && cur[r].stop;
+            sum += cur[r].iter;
+        }
+        if (all) break;
+        // every batch advances some right-hand side unless all are frozen; a
+        // state that neither advances nor stops is a logic error, not a hang
+        idle = (sum == last_sum) ? idle + 1 : 0;
+        last_sum = sum;
         if (idle >= 2) {
             st = set_error(PLQ_ERR_STATE, "inner iteration made no progress");
             break;
         }
     }
     cudaGraphExecDestroy(exec);
-    *final_state = cur;
     return st;
 }
 
@@ -174,21 +186,29 @@ plq_status parse(const plq_solver_params *p, Params *o) {
     return PLQ_OK;
 }
 
-// s = bhat - Mhat x_e (FP64); returns ||s||^2
+// s = bhat - Mhat x_e (FP64); per right-hand side |s|^2
 plq_status true_residual(Solve &S, void *s64, void *tmp_o64, const void *bhat, const void *xe, double *s2) {
     PLQ_TRY(hop(S, PLQ_F64, 1, tmp_o64, xe, EPI_PLAIN, 0, nullptr, 0.0));
-    PLQ_TRY(blas_copy_convert(S.Vh, s64, PLQ_F64, xe, PLQ_F64, S.s));
-    PLQ_TRY(blas_xpay64(S.Vh, bhat, -1.0, s64, S.s));  // s = bhat - x_e
+    PLQ_TRY(blas_copy_convert(S.N, s64, PLQ_F64, xe, PLQ_F64, S.s));
+    PLQ_TRY(blas_xpay64(S.N, bhat, -1.0, s64, S.s));  // s = bhat - x_e
     PLQ_TRY(hop(S, PLQ_F64, 0, s64, tmp_o64, EPI_XPAY_NORM, 0, s64, S.kappa * S.kappa));
-    return read_sums(S, s2, 1);
+    return read_sums(S, s2, S.n);
+}
+
+// zero right-hand side r of an FP64 half field of N elements (n interleaved)
+__global__ void zero_rhs_kernel(long long N, int n, int r, double2 *f) {
+    for (long long e = r + (long long)n * (blockIdx.x * (long long)blockDim.x + threadIdx.x); e < N;
+         e += (long long)n * gridDim.x * blockDim.x)
+        for (int k = 0; k < 12; ++k) f[k * N + e] = make_double2(0.0, 0.0);
 }
 
 enum { SOLVER_CG = 0, SOLVER_BICGSTAB = 1 };
 
-plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, const plq_solver_params *pp,
-                      plq_solve_info *info, void *stream, int method) {
-    if (info) std::memset(info, 0, sizeof(*info));
+plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, const plq_solver_params *pp,
+                      plq_solve_info *infos, void *stream, int method) {
+    if (infos && n > 0 && n <= PLQ_MAX_RHS) std::memset(infos, 0, sizeof(plq_solve_info) * n);
     if (!c) return set_error(PLQ_ERR_ARG, "null context");
+    if (n < 1 || n > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
     if (!x || !b || (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(b) & 15))
         return set_error(PLQ_ERR_ARG, "null or misaligned field pointer");
     if (x == b) return set_error(PLQ_ERR_ARG, "x and b must not overlap");
@@ -196,19 +216,20 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, const pl
     Params P;
     PLQ_TRY(parse(pp, &P));
     if (!c->gauge[PLQ_F64].ptr) return set_error(PLQ_ERR_STATE, "solvers need the FP64 gauge copy");
-    if (!c->gauge[P.inner].ptr)
-        return set_error(PLQ_ERR_STATE, "no gauge copy for inner precision %d", P.inner);
+    if (!c->gauge[P.inner].ptr) return set_error(PLQ_ERR_STATE, "no gauge copy for inner precision %d", P.inner);
     PLQ_CUDA(cudaSetDevice(c->device));
 
     Solve S;
     S.c = c;
     S.Vh = c->lat.Vh;
+    S.n = n;
+    S.N = (long long)S.Vh * n;
     S.kappa = kappa;
     S.P = P.inner;
     S.PX = P.inner == PLQ_F64 ? PLQ_F64 : PLQ_F32;
-    const size_t h64 = spinor_site_bytes(PLQ_F64) * S.Vh;
-    const size_t hL = spinor_site_bytes(S.P) * S.Vh;
-    const size_t hX = spinor_site_bytes(S.PX) * S.Vh;
+    const size_t h64 = spinor_site_bytes(PLQ_F64) * (size_t)S.N;
+    const size_t hL = spinor_site_bytes(S.P) * (size_t)S.N;
+    const size_t hX = spinor_site_bytes(S.PX) * (size_t)S.N;
     const int nL = method == SOLVER_CG ? 5 : 7;
     const size_t need = 5 * h64 + nL * hL + hX + 4096;
     PLQ_TRY(ensure_work(c, need));
@@ -243,87 +264,101 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, const pl
     const char *be = static_cast<const char *>(b), *bo = be + h64;
     char *xe = static_cast<char *>(x), *xo = xe + h64;
     plq_status st = PLQ_OK;
-    double n_e = 0, n_o = 0;
-    int iters = 0, n_rel = 0;
-    int result = PLQ_OK;
-    double true_rel = 0.0;
+    std::vector<double> n_e(n), n_o(n), bnorm2(n), bnorm(n), s2(n), r2(n), true_rel(n, 0.0);
+    std::vector<double> sigma(n, 0.5), last_rho(n, 0.0), best(n, INFINITY), target2(n, 0.0);
+    std::vector<int> iters(n, 0), n_rel(n, 0), stall(n, 0), done(n, 0), result(n, PLQ_OK);
+    std::vector<std::string> msg(n);
+    std::vector<SolverState> init(n), fin(n);
+    bool first = true;
 
     do {
-        if ((st = norm2_64(S, be, &n_e)) != PLQ_OK) break;
-        if ((st = norm2_64(S, bo, &n_o)) != PLQ_OK) break;
-        const double bnorm2 = n_e + n_o;
-        if (!std::isfinite(bnorm2)) {
-            result = set_error(PLQ_ERR_NAN, "source contains NaN or Inf");
-            break;
+        if ((st = norm2_64(S, be, n_e.data())) != PLQ_OK) break;
+        if ((st = norm2_64(S, bo, n_o.data())) != PLQ_OK) break;
+        if (!P.use_x0 && (st = blas_zero(S.N, xe, PLQ_F64, s)) != PLQ_OK) break;
+        for (int r = 0; r < n; ++r) {
+            bnorm2[r] = n_e[r] + n_o[r];
+            bnorm[r] = std::sqrt(bnorm2[r]);
+            if (!std::isfinite(bnorm2[r])) {
+                done[r] = 1;
+                result[r] = PLQ_ERR_NAN;
+                msg[r] = "source contains NaN or Inf";
+            } else if (bnorm2[r] == 0.0) {
+                // zero source: x = 0 exactly
+                done[r] = 1;
+                zero_rhs_kernel<<<256, 256, 0, s>>>(S.N, n, r, static_cast<double2 *>(static_cast<void *>(xe)));
+                if (method == SOLVER_BICGSTAB) {
+                    result[r] = PLQ_ERR_BREAKDOWN;
+                    msg[r] = "BiCGstab breakdown: rho = <rhat, r0> = 0 (zero source)";
+                }
+            }
         }
-        if (bnorm2 == 0.0) {
-            st = blas_zero(S.Vh, xe, PLQ_F64, s);
-            if (st == PLQ_OK) st = blas_zero(S.Vh, xo, PLQ_F64, s);
-            if (method == SOLVER_BICGSTAB && st == PLQ_OK)
-                result = set_error(PLQ_ERR_BREAKDOWN, "BiCGstab breakdown: rho = <rhat, r0> = 0 (zero source)");
-            break;
-        }
-        const double bnorm = std::sqrt(bnorm2);
         // bhat = b_e + kappa H_eo b_o
         if ((st = hop(S, PLQ_F64, 0, bhat, bo, EPI_XPAY, 0, be, kappa)) != PLQ_OK) break;
-        if (!P.use_x0 && (st = blas_zero(S.Vh, xe, PLQ_F64, s)) != PLQ_OK) break;
 
         const double delta = S.P == PLQ_F64 ? 0.0 : P.delta;
-        double sigma = 0.5;  // safety factor on the estimated inner target
-        double last_rho = 0.0;  // |r|^2 of the second-to-last iteration of the last inner CG run
-        double best = INFINITY;
-        int stall = 0;
-        bool first = true;
         for (;;) {
-            double s2 = 0;
-            if ((st = true_residual(S, s64, tmp_o64, bhat, xe, &s2)) != PLQ_OK) break;
-            if (!std::isfinite(s2)) {
-                result = set_error(PLQ_ERR_NAN, "NaN in the FP64 residual");
-                break;
+            if ((st = true_residual(S, s64, tmp_o64, bhat, xe, s2.data())) != PLQ_OK) break;
+            bool all_done = true;
+            for (int r = 0; r < n; ++r) {
+                if (done[r]) continue;
+                if (!std::isfinite(s2[r])) {
+                    done[r] = 1;
+                    result[r] = PLQ_ERR_NAN;
+                    msg[r] = "NaN in the FP64 residual";
+                    continue;
+                }
+                true_rel[r] = std::sqrt(s2[r]) / bnorm[r];
+                if (true_rel[r] <= P.tol) {
+                    done[r] = 1;
+                    continue;
+                }
+                if (iters[r] >= P.maxit) {
+                    done[r] = 1;
+                    result[r] = PLQ_ERR_NOT_CONVERGED;
+                    msg[r] = "no convergence within maxit";
+                    continue;
+                }
+                if (s2[r] < 0.99 * best[r]) {
+                    best[r] = s2[r];
+                    stall[r] = 0;
+                } else if (++stall[r] >= 20) {
+                    done[r] = 1;
+                    result[r] = PLQ_ERR_NOT_CONVERGED;
+                    msg[r] = "residual stalled";
+                    continue;
+                }
+                all_done = false;
             }
-            true_rel = std::sqrt(s2) / bnorm;
-            if (true_rel <= P.tol) break;
-            if (iters >= P.maxit) {
-                result = set_error(PLQ_ERR_NOT_CONVERGED, "no convergence in %d iterations (residual %.3e)",
-                                   iters, true_rel);
-                break;
+            if (all_done) break;
+            for (int r = 0; r < n; ++r) {
+                std::memset(&init[r], 0, sizeof(SolverState));
+                init[r].iter = iters[r];
+                init[r].maxit = P.maxit;
+                init[r].stop = done[r];
             }
-            if (s2 < 0.99 * best) {
-                best = s2;
-                stall = 0;
-            } else if (++stall >= 20) {
-                result = set_error(PLQ_ERR_NOT_CONVERGED, "residual stalled at %.3e", true_rel);
-                break;
-            }
-            SolverState init;
-            std::memset(&init, 0, sizeof init);
-            init.iter = iters;
-            init.maxit = P.maxit;
-            init.tiny = 0.0;
-            double target2 = 0.0;
-            int start_iter = iters;
-            SolverState fin;
             if (method == SOLVER_CG) {
                 // r = Mhat^dag s, the residual of the normal equations
                 if ((st = hop(S, PLQ_F64, 1, tmp_o64, s64, EPI_PLAIN, 1, nullptr, 0.0)) != PLQ_OK) break;
                 if ((st = hop(S, PLQ_F64, 0, r64, tmp_o64, EPI_XPAY_NORM, 1, s64, -kappa * kappa)) != PLQ_OK) break;
-                double r2 = 0;
-                if ((st = read_sums(S, &r2, 1)) != PLQ_OK) break;
-                const double ratio = std::sqrt(r2 / s2);
+                if ((st = read_sums(S, r2.data(), n)) != PLQ_OK) break;
                 void *rL = L[0], *pL = L[1], *qL = L[2], *mpL = L[3], *toL = L[4];
-                if ((st = blas_copy_convert(S.Vh, rL, S.P, r64, PLQ_F64, s)) != PLQ_OK) break;
-                if ((st = blas_zero(S.Vh, xL, S.PX, s)) != PLQ_OK) break;
-                target2 = std::pow(sigma * ratio * P.tol * bnorm, 2);
-                init.rho = r2;
-                // Reliable update: the direction survives and the iteration goes on
-                // as if the recursive residual had been replaced by the true one:
-                // p = r_true + beta p, beta = |r_true|^2 / rho_k with rho_k the
-                // |r|^2 of the iteration before the one that triggered.
-                init.beta = first ? 0.0 : r2 / last_rho;
-                init.stop_r2 = std::fmax(delta * delta * r2, target2);
-                if ((st = put_state(S, init)) != PLQ_OK) break;
-                if (first) st = blas_copy_convert(S.Vh, pL, S.P, rL, S.P, s);
-                else st = blas_cg_direction(S.Vh, pL, rL, S.P, c->state, s);
+                if ((st = blas_copy_convert(S.N, rL, S.P, r64, PLQ_F64, s)) != PLQ_OK) break;
+                if ((st = blas_zero(S.N, xL, S.PX, s)) != PLQ_OK) break;
+                for (int r = 0; r < n; ++r) {
+                    if (done[r]) continue;
+                    const double ratio = std::sqrt(r2[r] / s2[r]);
+                    target2[r] = std::pow(sigma[r] * ratio * P.tol * bnorm[r], 2);
+                    init[r].rho = r2[r];
+                    // Reliable update: the direction survives and the iteration goes on
+                    // as if the recursive residual had been replaced by the true one:
+                    // p = r_true + beta p, beta = |r_true|^2 / rho_k with rho_k the
+                    // |r|^2 of the iteration before the one that triggered.
+                    init[r].beta = first ? 0.0 : r2[r] / last_rho[r];
+                    init[r].stop_r2 = std::fmax(delta * delta * r2[r], target2[r]);
+                }
+                if ((st = put_states(S, init)) != PLQ_OK) break;
+                if (first) st = blas_copy_convert(S.N, pL, S.P, rL, S.P, s);
+                else st = blas_cg_direction(S.N, n, pL, rL, S.P, c->state, s);
                 if (st != PLQ_OK) break;
                 const double kk = kappa * kappa;
                 const int PI = S.P;
@@ -333,71 +368,82 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, const pl
                     PLQ_TRY(hop(S, PI, 1, toL, mpL, EPI_PLAIN, 1, nullptr, 0.0, FIN_NONE, nullptr, true));
                     PLQ_TRY(hop(S, PI, 0, qL, toL, EPI_XPAY, 1, mpL, -kk, FIN_NONE, nullptr, true));
                     Reduce rb = reduce_of(c, FIN_CG_BETA);
-                    PLQ_TRY(blas_cg_update(S.Vh, xL, rL, pL, qL, PI, rb, c->state, s));
-                    return blas_cg_direction(S.Vh, pL, rL, PI, c->state, s);
+                    PLQ_TRY(blas_cg_update(S.N, n, xL, rL, pL, qL, PI, rb, c->state, s));
+                    return blas_cg_direction(S.N, n, pL, rL, PI, c->state, s);
                 };
-                if ((st = run_batches(S, P.k, body, &fin)) != PLQ_OK) break;
+                if ((st = run_batches(S, P.k, body, fin)) != PLQ_OK) break;
             } else {
                 void *rL = L[0], *rhL = L[1], *pL = L[2], *vL = L[3], *sL = L[4], *tL = L[5], *toL = L[6];
-                if ((st = blas_copy_convert(S.Vh, rL, S.P, s64, PLQ_F64, s)) != PLQ_OK) break;
-                if ((st = blas_copy_convert(S.Vh, rhL, S.P, rL, S.P, s)) != PLQ_OK) break;
-                if ((st = blas_copy_convert(S.Vh, pL, S.P, rL, S.P, s)) != PLQ_OK) break;
-                if ((st = blas_zero(S.Vh, xL, S.PX, s)) != PLQ_OK) break;
-                target2 = std::pow(sigma * P.tol * bnorm, 2);
-                init.c_rho = make_double2(s2, 0.0);
-                init.stop_r2 = std::fmax(delta * delta * s2, target2);
-                init.tiny = 1e-300;
-                if ((st = put_state(S, init)) != PLQ_OK) break;
+                if ((st = blas_copy_convert(S.N, rL, S.P, s64, PLQ_F64, s)) != PLQ_OK) break;
+                if ((st = blas_copy_convert(S.N, rhL, S.P, rL, S.P, s)) != PLQ_OK) break;
+                if ((st = blas_copy_convert(S.N, pL, S.P, rL, S.P, s)) != PLQ_OK) break;
+                if ((st = blas_zero(S.N, xL, S.PX, s)) != PLQ_OK) break;
+                for (int r = 0; r < n; ++r) {
+                    if (done[r]) continue;
+                    target2[r] = std::pow(sigma[r] * P.tol * bnorm[r], 2);
+                    init[r].c_rho = make_double2(s2[r], 0.0);
+                    init[r].stop_r2 = std::fmax(delta * delta * s2[r], target2[r]);
+                    init[r].tiny = 1e-300;
+                }
+                if ((st = put_states(S, init)) != PLQ_OK) break;
                 const double kk = kappa * kappa;
                 const int PI = S.P;
                 auto body = [&]() -> plq_status {
                     PLQ_TRY(hop(S, PI, 1, toL, pL, EPI_PLAIN, 0, nullptr, 0.0, FIN_NONE, nullptr, true));
                     PLQ_TRY(hop(S, PI, 0, vL, toL, EPI_XPAY_DOTW, 0, pL, -kk, FIN_BICG_ALPHA, rhL, true));
-                    PLQ_TRY(blas_bicg_s(S.Vh, sL, rL, vL, PI, c->state, s));
+                    PLQ_TRY(blas_bicg_s(S.N, n, sL, rL, vL, PI, c->state, s));
                     PLQ_TRY(hop(S, PI, 1, toL, sL, EPI_PLAIN, 0, nullptr, 0.0, FIN_NONE, nullptr, true));
                     PLQ_TRY(hop(S, PI, 0, tL, toL, EPI_XPAY_TS, 0, sL, -kk, FIN_BICG_OMEGA, nullptr, true));
                     Reduce rb = reduce_of(c, FIN_BICG_RHO);
-                    PLQ_TRY(blas_bicg_update(S.Vh, xL, rL, pL, sL, tL, rhL, PI, rb, c->state, s));
-                    return blas_bicg_p(S.Vh, pL, rL, vL, PI, c->state, s);
+                    PLQ_TRY(blas_bicg_update(S.N, n, xL, rL, pL, sL, tL, rhL, PI, rb, c->state, s));
+                    return blas_bicg_p(S.N, n, pL, rL, vL, PI, c->state, s);
                 };
-                if ((st = run_batches(S, P.k, body, &fin)) != PLQ_OK) break;
+                if ((st = run_batches(S, P.k, body, fin)) != PLQ_OK) break;
             }
-            const int done = fin.iter - start_iter;
-            S.hops += 4.0 * done;
-            iters = fin.iter;
-            if (fin.flags & FLAG_NAN) {
-                result = set_error(PLQ_ERR_NAN, "NaN or Inf in the inner iteration");
-                break;
+            for (int r = 0; r < n; ++r) {
+                if (done[r]) continue;
+                const int progressed = fin[r].iter - iters[r];
+                iters[r] = fin[r].iter;
+                if (fin[r].flags & FLAG_NAN) {
+                    done[r] = 1;
+                    result[r] = PLQ_ERR_NAN;
+                    msg[r] = "NaN or Inf in the inner iteration";
+                } else if ((fin[r].flags & FLAG_BREAKDOWN) && progressed == 0) {
+                    done[r] = 1;
+                    result[r] = PLQ_ERR_BREAKDOWN;
+                    msg[r] = "Krylov breakdown (rho or omega vanished)";
+                }
+                ++n_rel[r];
+                // the inner target was reached but the FP64 check may still fail:
+                // tighten the estimate for the next round
+                const double fr = method == SOLVER_CG ? fin[r].rho : fin[r].r2;
+                if (fr <= target2[r] * 1.0000001) sigma[r] *= 0.25;
+                // FIN_CG_BETA left rho = rho_{k+1} and beta = rho_{k+1} / rho_k
+                last_rho[r] = fin[r].beta > 0.0 ? fin[r].rho / fin[r].beta : fin[r].rho;
             }
-            if ((fin.flags & FLAG_BREAKDOWN) && done == 0) {
-                result = set_error(PLQ_ERR_BREAKDOWN, "Krylov breakdown (rho or omega vanished)");
-                break;
-            }
-            // reliable update: x_e += x_inner (FP64)
-            if ((st = blas_accumulate(S.Vh, xe, xL, S.PX, s)) != PLQ_OK) break;
-            ++n_rel;
+            // reliable update: x_e += x_inner (FP64); frozen right-hand sides add zero
+            if ((st = blas_accumulate(S.N, xe, xL, S.PX, s)) != PLQ_OK) break;
             first = false;
-            // the inner target was reached but the FP64 check may still fail:
-            // tighten the estimate for the next round
-            const double fr = method == SOLVER_CG ? fin.rho : fin.r2;
-            // FIN_CG_BETA left rho = rho_{k+1} and beta = rho_{k+1} / rho_k
-            last_rho = fin.beta > 0.0 ? fin.rho / fin.beta : fin.rho;
-            if (fr <= target2 * 1.0000001) sigma *= 0.25;
         }
-        if (st != PLQ_OK || result != PLQ_OK) break;
+        if (st != PLQ_OK) break;
         // x_o = b_o + kappa H_oe x_e
         if ((st = hop(S, PLQ_F64, 1, xo, xe, EPI_XPAY, 0, bo, kappa)) != PLQ_OK) break;
         // full true residual ||b - M x|| with the FP64 operator, both parities
-        double re = 0, ro = 0;
+        std::vector<double> re(n), ro(n);
         if ((st = hop(S, PLQ_F64, 0, t64, xo, EPI_XPAY, 0, xe, -kappa)) != PLQ_OK) break;
-        if ((st = blas_xpay64(S.Vh, be, -1.0, t64, s)) != PLQ_OK) break;
-        if ((st = norm2_64(S, t64, &re)) != PLQ_OK) break;
+        if ((st = blas_xpay64(S.N, be, -1.0, t64, s)) != PLQ_OK) break;
+        if ((st = norm2_64(S, t64, re.data())) != PLQ_OK) break;
         if ((st = hop(S, PLQ_F64, 1, tmp_o64, xe, EPI_XPAY, 0, xo, -kappa)) != PLQ_OK) break;
-        if ((st = blas_xpay64(S.Vh, bo, -1.0, tmp_o64, s)) != PLQ_OK) break;
-        if ((st = norm2_64(S, tmp_o64, &ro)) != PLQ_OK) break;
-        true_rel = std::sqrt((re + ro) / bnorm2);
-        if (!(true_rel <= P.tol) && result == PLQ_OK)
-            result = set_error(PLQ_ERR_NOT_CONVERGED, "final residual %.3e above tol %.3e", true_rel, P.tol);
+        if ((st = blas_xpay64(S.N, bo, -1.0, tmp_o64, s)) != PLQ_OK) break;
+        if ((st = norm2_64(S, tmp_o64, ro.data())) != PLQ_OK) break;
+        for (int r = 0; r < n; ++r) {
+            if (bnorm2[r] == 0.0 || !std::isfinite(bnorm2[r])) continue;
+            true_rel[r] = std::sqrt((re[r] + ro[r]) / bnorm2[r]);
+            if (!(true_rel[r] <= P.tol) && result[r] == PLQ_OK) {
+                result[r] = PLQ_ERR_NOT_CONVERGED;
+                msg[r] = "final residual above tol";
+            }
+        }
     } while (0);
 
     cudaError_t e1 = cudaEventRecord(ev1, s);
@@ -406,14 +452,25 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, const pl
     auto wall1 = std::chrono::steady_clock::now();
     cleanup();
     if (st == PLQ_OK && e1 != cudaSuccess) st = cuda_error(e1, "solver completion");
-    const int status = st != PLQ_OK ? st : result;
-    if (info) {
-        info->status = status;
-        info->iterations = iters;
-        info->n_reliable = n_rel;
-        info->true_rel_residual = true_rel;
-        info->seconds = std::chrono::duration<double>(wall1 - wall0).count();
-        info->hop_applications = S.hops;
+    int status = st;
+    if (status == PLQ_OK) {
+        for (int r = 0; r < n; ++r)
+            if (result[r] != PLQ_OK) {
+                status = set_error(result[r], "rhs %d: %s (residual %.3e after %d iterations)", r, msg[r].c_str(),
+                                   true_rel[r], iters[r]);
+                break;
+            }
+    }
+    if (infos) {
+        const double secs = std::chrono::duration<double>(wall1 - wall0).count();
+        for (int r = 0; r < n; ++r) {
+            infos[r].status = st != PLQ_OK ? st : result[r];
+            infos[r].iterations = iters[r];
+            infos[r].n_reliable = n_rel[r];
+            infos[r].true_rel_residual = true_rel[r];
+            infos[r].seconds = secs;
+            infos[r].hop_applications = S.hops + 4.0 * iters[r];
+        }
     }
     return status;
 }
@@ -425,12 +482,22 @@ extern "C" {
 
 plq_status plq_cg_solve(plq_ctx *ctx, void *x, const void *b, double kappa, const plq_solver_params *params,
                         plq_solve_info *info, void *stream) {
-    return plq::solve_impl(ctx, x, b, kappa, params, info, stream, plq::SOLVER_CG);
+    return plq::solve_impl(ctx, x, b, kappa, 1, params, info, stream, plq::SOLVER_CG);
 }
 
 plq_status plq_bicgstab_solve(plq_ctx *ctx, void *x, const void *b, double kappa, const plq_solver_params *params,
                               plq_solve_info *info, void *stream) {
-    return plq::solve_impl(ctx, x, b, kappa, params, info, stream, plq::SOLVER_BICGSTAB);
+    return plq::solve_impl(ctx, x, b, kappa, 1, params, info, stream, plq::SOLVER_BICGSTAB);
+}
+
+plq_status plq_cg_solve_multi(plq_ctx *ctx, void *x, const void *b, double kappa, int nrhs,
+                              const plq_solver_params *params, plq_solve_info *infos, void *stream) {
+    return plq::solve_impl(ctx, x, b, kappa, nrhs, params, infos, stream, plq::SOLVER_CG);
+}
+
+plq_status plq_bicgstab_solve_multi(plq_ctx *ctx, void *x, const void *b, double kappa, int nrhs,
+                                    const plq_solver_params *params, plq_solve_info *infos, void *stream) {
+    return plq::solve_impl(ctx, x, b, kappa, nrhs, params, infos, stream, plq::SOLVER_BICGSTAB);
 }
 
 }  // extern "C"

@@ -91,6 +91,10 @@ SIGNATURES = {
     "plq_cg_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
     "plq_bicgstab_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams),
                                     ctypes.POINTER(SolveInfo), _vp]),
+    "plq_cg_solve_multi": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, ctypes.POINTER(SolverParams),
+                                    ctypes.POINTER(SolveInfo), _vp]),
+    "plq_bicgstab_solve_multi": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, ctypes.POINTER(SolverParams),
+                                          ctypes.POINTER(SolveInfo), _vp]),
     "plq_measure_fma_rate": (_c_int, [_c_int, _c_int, ctypes.POINTER(ctypes.c_double)]),
     "plq_schur_apply_noalloc": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, _c_int, _vp]),
     "plq_autotune": (_c_int, [_vp, _c_int, _c_int, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
@@ -303,6 +307,26 @@ class Context:
         """CG on the even-odd normal equations; x, b packed full FP64 fields."""
         return self._solve(lib().plq_cg_solve, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every,
                            stream, raise_on_error)
+
+    def _solve_multi(self, fn, x, b, kappa, nrhs, tol, maxit, inner_prec, delta, use_x0, check_every, stream,
+                     raise_on_error):
+        p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every)
+        infos = (SolveInfo * nrhs)()
+        st = fn(self._h, _ptr(x), _ptr(b), float(kappa), nrhs, ctypes.byref(p), infos, _stream(stream))
+        if raise_on_error:
+            check(st, list(infos))
+        return list(infos)
+
+    def cg_solve_multi(self, x, b, kappa, nrhs, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
+                       check_every=16, stream=None, raise_on_error=True):
+        """CG for nrhs interleaved right-hand sides (links loaded once per operator application)."""
+        return self._solve_multi(lib().plq_cg_solve_multi, x, b, kappa, nrhs, tol, maxit, inner_prec, delta, use_x0,
+                                 check_every, stream, raise_on_error)
+
+    def bicgstab_solve_multi(self, x, b, kappa, nrhs, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1,
+                             use_x0=False, check_every=16, stream=None, raise_on_error=True):
+        return self._solve_multi(lib().plq_bicgstab_solve_multi, x, b, kappa, nrhs, tol, maxit, inner_prec, delta,
+                                 use_x0, check_every, stream, raise_on_error)
 
     def bicgstab_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
                        check_every=16, stream=None, raise_on_error=True):

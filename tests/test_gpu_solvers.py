@@ -123,3 +123,64 @@ def test_missing_inner_gauge_copy():
         with pytest.raises(PLQError) as e:
             ctx.cg_solve(x, bd, 0.12, inner_prec=F16)
         assert e.value.status == plq.PLQ_ERR_STATE
+
+
+def run_multi(method, dims, eps, seed, kappa, inner, sources, **kw):
+    U = S.gauge_field(dims, eps, seed)
+    n = len(sources)
+    b = np.stack(sources)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        if inner != F64:
+            ctx.gauge_upload(U, 12, inner)
+        bd = ctx.to_device(b, F64, n)
+        x = ctx.empty_full(F64, n)
+        fn = ctx.cg_solve_multi if method == "cg" else ctx.bicgstab_solve_multi
+        infos = fn(x, bd, kappa, n, inner_prec=inner, **kw)
+        xs = ctx.to_host(x, F64, n).reshape((n,) + b.shape[1:])
+    return U, b, xs, infos
+
+
+@pytest.mark.parametrize("method", ["cg", "bicgstab"])
+@pytest.mark.parametrize("inner", [F64, F32, F16])
+def test_multi_rhs_point_sources(method, inner):
+    # the spin x colour columns of a point-source propagator, solved together
+    dims = (16, 8, 8, 8)
+    kappa = 0.121
+    srcs = [S.point_source(dims, s, c) for s in range(4) for c in range(3)]
+    U, b, x, infos = run_multi(method, dims, 0.25, 4, kappa, inner, srcs)
+    for r in range(12):
+        res = oracle_residual(U, b[r], x[r], kappa)
+        assert res <= 1e-10, (r, res, infos[r].as_dict())
+        assert abs(infos[r].true_rel_residual - res) < 1e-11
+
+
+def test_multi_rhs_matches_single_solves():
+    dims = (8, 4, 4, 4)
+    kappa = 0.12
+    srcs = [S.gaussian_spinor(dims, 40 + r) for r in range(3)]
+    U, b, x, infos = run_multi("cg", dims, 0.3, 7, kappa, F32, srcs)
+    for r in range(3):
+        assert oracle_residual(U, b[r], x[r], kappa) <= 1e-10
+    # each right-hand side's solution is the single solve of that source
+    U1 = S.gauge_field(dims, 0.3, 7)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U1, 18, F64)
+        ctx.gauge_upload(U1, 12, F32)
+        for r in range(3):
+            bd = ctx.to_device(srcs[r], F64)
+            xd = ctx.empty_full(F64)
+            ctx.cg_solve(xd, bd, kappa, inner_prec=F32)
+            x1 = ctx.to_host(xd, F64)
+            assert np.linalg.norm(x1 - x[r]) / np.linalg.norm(x1) < 1e-8
+
+
+def test_multi_rhs_zero_and_nonzero_sources():
+    dims = (8, 4, 4, 4)
+    kappa = 0.12
+    srcs = [S.gaussian_spinor(dims, 50), np.zeros(S.lattice_shape(dims) + (4, 3), complex),
+            S.gaussian_spinor(dims, 51)]
+    U, b, x, infos = run_multi("cg", dims, 0.3, 8, kappa, F32, srcs)
+    assert np.all(x[1] == 0) and infos[1].iterations == 0
+    for r in (0, 2):
+        assert oracle_residual(U, b[r], x[r], kappa) <= 1e-10

@@ -43,3 +43,18 @@ def test_batch_specs():
     assert len(specs) == 16
     assert all(0.110 <= s["kappa"] <= 0.124 for s in specs)
     assert [s["dims"][0] for s in specs[:3]] == [16, 32, 48]
+
+
+def test_parallel_generation_matches_serial():
+    dims = (4, 4, 2, 2)
+    a = S.gauge_field(dims, 0.3, 5, workers=1)
+    b = S.gauge_field(dims, 0.3, 5, workers=2)
+    assert np.array_equal(a, b)
+    assert np.array_equal(S.gaussian_spinor(dims, 5, workers=1), S.gaussian_spinor(dims, 5, workers=2))
+
+
+def test_time_slices_are_independent_streams():
+    # slice t of a T=4 lattice equals slice t of a T=2 lattice with the same seed (t < 2)
+    a = S.gauge_field((4, 2, 2, 2), 0.3, 9)
+    b = S.gauge_field((2, 2, 2, 2), 0.3, 9)
+    assert np.array_equal(a[:2], b)

@@ -254,6 +254,7 @@ def propagator_section(torch, local_rank, quick):
         ops = {}
         for pname, prec, reals in [("f32", F32, 18), ("f32", F32, 12), ("f16", F16, 12)]:
             ctx.gauge_upload(U, reals, prec)
+            tuned = ctx.autotune(prec, n)
             inp = ctx.empty_half(prec, n)
             inp.zero_()
             o = ctx.empty_half(prec, n)
@@ -273,12 +274,14 @@ def propagator_section(torch, local_rank, quick):
             gbs = site_bytes * vh * n / (ms * 1e-3) / 1e9
             ops[f"{pname}_{reals}"] = {"ms": ms, "gflops": FLOP_PER_SITE * vh * n / (ms * 1e-3) / 1e9,
                                        "gbs_compulsory": gbs, "frac_of_measured_hbm": gbs / peak,
-                                       "bytes_per_site_rhs": site_bytes}
+                                       "bytes_per_site_rhs": site_bytes, "launch": tuned}
             log(f"[bench] multi-RHS {pname}-{reals} x{n}: {ms:.2f} ms, {gbs:.0f} GB/s")
             del inp, o
         out["operator_12rhs"] = ops
         ctx.gauge_upload(U, 18, F64)
         ctx.gauge_upload(U, 12, F32)
+        ctx.autotune(F32, n)
+        ctx.autotune(F32, 1)
         # 12 point sources, canonical layout, built on the device
         V = S.volume(dims)
         b = torch.zeros(n * V * 24, dtype=torch.float64, device=f"cuda:{local_rank}")
@@ -290,7 +293,7 @@ def propagator_section(torch, local_rank, quick):
         x = ctx.empty_full(F64, n)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        infos = ctx.cg_solve_multi(x, bd, kappa, n, tol=1e-10, inner_prec=F32, raise_on_error=False)
+        infos = ctx.cg_solve_multi(x, bd, kappa, n, tol=1e-10, inner_prec=F32, maxit=3000, raise_on_error=False)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         out["batched_cg_mixed_f32"] = {
@@ -310,7 +313,7 @@ def propagator_section(torch, local_rank, quick):
             x1 = ctx.empty_full(F64)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            info = ctx.cg_solve(x1, b1, kappa, tol=1e-10, inner_prec=F32, raise_on_error=False)
+            info = ctx.cg_solve(x1, b1, kappa, tol=1e-10, inner_prec=F32, maxit=3000, raise_on_error=False)
             torch.cuda.synchronize()
             singles.append((time.perf_counter() - t0, info.iterations, info.true_rel_residual))
             del bs, b1, x1

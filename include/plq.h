@@ -112,6 +112,8 @@ typedef struct {
                           default 0.1 (ignored when inner_prec == PLQ_F64)                  */
     int use_x0;        /* 1: x holds an initial guess on entry (resume); 0: start from 0   */
     int check_every;   /* inner iterations per host convergence poll, default 16           */
+    double mu;         /* twisted mass: solve M_tm = 1 - kappa H + 2 i kappa mu gamma5
+                          (0: the Wilson operator M)                                        */
 } plq_solver_params;
 
 /* Per-solve report. */
@@ -193,6 +195,16 @@ PLQ_API plq_status plq_hopping_eo_host(plq_ctx *ctx, int out_parity, void *out_h
  * precision `prec`, nrhs = 1; they must not overlap. */
 PLQ_API plq_status plq_wilson_apply(plq_ctx *ctx, void *out, const void *in, double kappa, int prec, void *stream);
 
+/* Twisted-mass Wilson operator (the fermions of the paper's Sec. 3 EigCG
+ * solves; the operator itself is the standard twisted-mass formulation the
+ * paper cites): out = M_tm in = in - kappa H in + 2 i kappa mu gamma5 in, on
+ * packed full fields of precision `prec`.  mu = 0 gives plq_wilson_apply.
+ * The solvers handle M_tm when plq_solver_params.mu != 0, with the Schur
+ * complement Mhat_tm = A - kappa^2 H_eo A^{-1} H_oe, A = 1 + 2 i kappa mu
+ * gamma5, and Mhat_tm(mu)^dagger = gamma5 Mhat_tm(-mu) gamma5. */
+PLQ_API plq_status plq_twisted_apply(plq_ctx *ctx, void *out, const void *in, double kappa, double mu, int prec,
+                                     void *stream);
+
 /* Even-odd Schur operator on even half fields: out = Mhat in =
  * in - kappa^2 H_eo H_oe in (dagger != 0: Mhat^dagger = gamma5 Mhat gamma5).
  * `tmp` is a caller-owned odd half field of the same precision. */
@@ -229,6 +241,34 @@ PLQ_API plq_status plq_cg_solve_multi(plq_ctx *ctx, void *x, const void *b, doub
 PLQ_API plq_status plq_bicgstab_solve_multi(plq_ctx *ctx, void *x, const void *b, double kappa, int nrhs,
                                             const plq_solver_params *params, plq_solve_info *infos, void *stream);
 
+/* Launch report of plq_cg_solve_batched. */
+typedef struct {
+    int grid;            /* blocks of the persistent kernel (all co-resident)  */
+    int block;           /* threads per block                                  */
+    int graph_captured;  /* 1 if the launch ran as a captured CUDA graph       */
+    int launches;        /* kernel launches of the solve (1 on success)        */
+    double seconds;      /* time of the persistent kernel                      */
+} plq_batch_info;
+
+/* Batched CG: n (1..64) independent systems M_k x_k = b_k -- different
+ * lattices (one context each, same device), kappas and iteration counts --
+ * solved by ONE persistent cooperative kernel launch, captured in a CUDA
+ * graph.  Each system runs the algorithm of plq_cg_solve (even-odd normal
+ * equations, inner precision params->inner_prec with FP64 reliable updates)
+ * as its own state machine; all systems advance in lockstep phases separated
+ * by grid-wide barriers, and the sites of every still-active system form one
+ * shared work range, so converged systems retire and their blocks move to the
+ * others.  Barriers wait with a time limit (about 5 s) and report
+ * PLQ_ERR_TIMEOUT instead of hanging.  Each context needs an 18-real FP64
+ * gauge copy and a copy of the inner precision (the same link format for all
+ * systems; FP16 inner solves use 12-real links).  x[k], b[k]: packed full
+ * FP64 fields of context k.  infos (n entries) and binfo may be NULL.  After
+ * the kernel every system's true residual is recomputed with the FP64
+ * operator; the call returns PLQ_OK only if all are <= tol. */
+PLQ_API plq_status plq_cg_solve_batched(plq_ctx **ctxs, int n, void **x, const void **b, const double *kappa,
+                                        const plq_solver_params *params, plq_solve_info *infos,
+                                        plq_batch_info *binfo, void *stream);
+
 /* Allocation-free Schur operator.  No counterpart in the paper: this is a
  * service to callers that cannot allocate device memory at the moment they
  * apply the operator -- code running while a CUDA graph is being captured
@@ -261,6 +301,7 @@ PLQ_API plq_status plq_schur_apply_noalloc(plq_ctx *ctx, void *out, const void *
 typedef struct {
     int block;            /* threads per block chosen                                      */
     int index_mode;       /* 0: neighbours from coordinates; 1: precomputed neighbour table */
+    int rhs_tile;         /* right-hand sides per thread (each loaded link serves all)     */
     double us_per_launch; /* measured time of one half-lattice application                 */
     int from_cache;       /* 1 if the choice came from the cache file                      */
     int candidates;       /* configurations timed                                          */
@@ -270,7 +311,10 @@ typedef struct {
  * right-hand sides: times every threads-per-block value in {64, 96, 128, 192,
  * 256} with neighbour indices computed inline from the coordinates and read
  * from a precomputed per-site table (the pointer-array addressing the paper
- * describes for out-of-order site access, Sec. 2.2), and keeps the fastest in
+ * describes for out-of-order site access, Sec. 2.2), and for nrhs > 1 (FP32
+ * and FP16 storage) with 2 or 4 right-hand sides per thread (register tiles
+ * that reuse each loaded link, Sec. 2.3's one-matrix-two-vectors idea
+ * widened), and keeps the fastest in
  * the context for every later operator and solver call of that precision.
  * cache_path (NULL: the PLQ_TUNE_CACHE environment variable, if set) names a
  * text file keyed by GPU name, lattice, precision, link format and nrhs: a
@@ -281,8 +325,8 @@ PLQ_API plq_status plq_autotune(plq_ctx *ctx, int prec, int nrhs, const char *ca
 
 /* Set the hopping launch of (prec, nrhs) by hand: block = threads per block
  * (0 = library default, else a multiple of 32 up to 256), index_mode 0 or 1
- * as above. */
-PLQ_API plq_status plq_set_launch(plq_ctx *ctx, int prec, int nrhs, int block, int index_mode);
+ * and rhs_tile 1, 2 or 4 (dividing nrhs) as above. */
+PLQ_API plq_status plq_set_launch(plq_ctx *ctx, int prec, int nrhs, int block, int index_mode, int rhs_tile);
 
 /* Roofline calibration (a measurement helper; the paper has no counterpart):
  * the sustained FMA throughput of the CUDA cores of `device` in FP64

@@ -184,6 +184,62 @@ def norm(a):
 
 
 # --------------------------------------------------------------------------
+# Twisted-mass Wilson operator (Sec. 3: the tmLQCD solves use twisted-mass fermions)
+# --------------------------------------------------------------------------
+# The paper does not print the operator; the reading is the standard one of
+# the twisted-mass formulation it cites (Frezzotti et al.): in the hopping
+# normalisation M_tm = 1 - kappa H + 2 i kappa mu gamma5.
+def twisted(U, phi, kappa, mu, t_bc=-1):
+    """M_tm phi = phi - kappa H phi + 2 i kappa mu gamma5 phi."""
+    return wilson(U, phi, kappa, t_bc) + 2j * kappa * mu * gamma5(phi)
+
+
+def twist_diag(phi, kappa, mu, inverse=False):
+    """The site-diagonal part A = 1 + 2 i kappa mu gamma5 (or its inverse)."""
+    nu = 2 * kappa * mu
+    if inverse:
+        return (phi - 1j * nu * gamma5(phi)) / (1 + nu * nu)
+    return phi + 1j * nu * gamma5(phi)
+
+
+def schur_tm(U, v_e, kappa, mu, t_bc=-1):
+    """Mhat_tm v_e = A v_e - kappa^2 H_eo A^{-1} H_oe v_e (A = 1 + 2 i kappa mu gamma5)."""
+    v_e = restrict(v_e, 0)
+    inner = twist_diag(hop_eo(U, v_e, 1, t_bc), kappa, mu, inverse=True)
+    return twist_diag(v_e, kappa, mu) - kappa * kappa * hop_eo(U, inner, 0, t_bc)
+
+
+def schur_tm_rhs(U, b, kappa, mu, t_bc=-1):
+    """bhat_e = b_e + kappa H_eo A^{-1} b_o."""
+    return restrict(b, 0) + kappa * hop_eo(U, twist_diag(restrict(b, 1), kappa, mu, inverse=True), 0, t_bc)
+
+
+def reconstruct_odd_tm(U, x_e, b, kappa, mu, t_bc=-1):
+    """x_o = A^{-1} (b_o + kappa H_oe x_e)."""
+    return twist_diag(restrict(b, 1) + kappa * hop_eo(U, x_e, 1, t_bc), kappa, mu, inverse=True)
+
+
+def solve_cg_eo_tm(U, b, kappa, mu, tol=1e-10, maxit=20000, t_bc=-1, check_every=10):
+    """M_tm x = b by CG on Mhat_tm^dag Mhat_tm, with Mhat_tm(mu)^dag = gamma5 Mhat_tm(-mu) gamma5."""
+    bhat = schur_tm_rhs(U, b, kappa, mu, t_bc)
+    bnorm = norm(b)
+    Mh = lambda v: schur_tm(U, v, kappa, mu, t_bc)
+    Mhd = lambda v: gamma5(schur_tm(U, gamma5(v), kappa, -mu, t_bc))
+    state = {"n": 0}
+
+    def check(x, rnorm):
+        state["n"] += 1
+        if state["n"] % check_every:
+            return False
+        return norm(bhat - Mh(x)) <= tol * bnorm
+
+    x_e, it, hist = cg(lambda v: Mhd(Mh(v)), Mhd(bhat), None, 0.0, maxit, check)
+    x = restrict(x_e, 0) + reconstruct_odd_tm(U, x_e, b, kappa, mu, t_bc)
+    rel = norm(b - twisted(U, x, kappa, mu, t_bc)) / bnorm
+    return SolveResult(x, it, "ok" if rel <= tol else "not_converged", rel, hist)
+
+
+# --------------------------------------------------------------------------
 # Solvers
 # --------------------------------------------------------------------------
 class SolveResult:

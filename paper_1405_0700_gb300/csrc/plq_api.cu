@@ -25,18 +25,22 @@ plq_status cuda_error(cudaError_t e, const char *what) {
                      cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
-plq_status launch_hop_f64(const HopArgs &a, int reals, int epi, cudaStream_t s, int block);
-plq_status launch_hop_f32(const HopArgs &a, int reals, int epi, cudaStream_t s, int block);
-plq_status launch_hop_f16(const HopArgs &a, int reals, int epi, cudaStream_t s, int block);
+plq_status launch_hop_f64_18(const HopArgs &a, int epi, cudaStream_t s, int block);
+plq_status launch_hop_f64_12(const HopArgs &a, int epi, cudaStream_t s, int block);
+plq_status launch_hop_f32_18(const HopArgs &a, int epi, cudaStream_t s, int block);
+plq_status launch_hop_f32_12(const HopArgs &a, int epi, cudaStream_t s, int block);
+plq_status launch_hop_f16_18(const HopArgs &a, int epi, cudaStream_t s, int block);
+plq_status launch_hop_f16_12(const HopArgs &a, int epi, cudaStream_t s, int block);
 
 int hop_default_block(int prec) { return prec == PLQ_F64 ? 128 : 128; }
 
 plq_status launch_hop(const HopArgs &a, int prec, int reals, int epi, cudaStream_t s) {
     const int block = a.block > 0 ? a.block : hop_default_block(prec);
+    const bool r12 = reals == 12;
     switch (prec) {
-    case PLQ_F64: return launch_hop_f64(a, reals, epi, s, block);
-    case PLQ_F32: return launch_hop_f32(a, reals, epi, s, block);
-    case PLQ_F16: return launch_hop_f16(a, reals, epi, s, block);
+    case PLQ_F64: return r12 ? launch_hop_f64_12(a, epi, s, block) : launch_hop_f64_18(a, epi, s, block);
+    case PLQ_F32: return r12 ? launch_hop_f32_12(a, epi, s, block) : launch_hop_f32_18(a, epi, s, block);
+    case PLQ_F16: return r12 ? launch_hop_f16_12(a, epi, s, block) : launch_hop_f16_18(a, epi, s, block);
     default: return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
     }
 }
@@ -50,6 +54,15 @@ plq_status ensure_work(Ctx *c, size_t bytes) {
     }
     PLQ_CUDA(cudaMalloc(&c->work, bytes));
     c->work_bytes = bytes;
+    return PLQ_OK;
+}
+
+plq_status ensure_pipeline(Ctx *c) {
+    if (c->copy_in) return PLQ_OK;
+    PLQ_CUDA(cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking));
+    PLQ_CUDA(cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking));
+    PLQ_CUDA(cudaStreamCreateWithFlags(&c->compute, cudaStreamNonBlocking));
+    for (auto &e : c->ev) PLQ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return PLQ_OK;
 }
 
@@ -168,6 +181,11 @@ plq_status plq_finalize(plq_ctx *c) {
     if (c->state_host) cudaFreeHost(c->state_host);
     if (c->work) cudaFree(c->work);
     if (c->stage) cudaFree(c->stage);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->copy_in) cudaStreamDestroy(c->copy_in);
+    if (c->copy_out) cudaStreamDestroy(c->copy_out);
+    if (c->compute) cudaStreamDestroy(c->compute);
     delete c;
     return PLQ_OK;
 }
@@ -279,13 +297,55 @@ plq_status plq_hopping_eo_host(plq_ctx *c, int out_parity, void *out_host, const
     PLQ_TRY(use_device(c));
     const size_t bytes = plq_field_bytes(c, prec, nrhs);
     PLQ_TRY(ensure_stage(c, 2 * bytes));
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PLQ_TRY(ensure_pipeline(c));
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
     char *din = static_cast<char *>(c->stage), *dout = din + bytes;
-    PLQ_CUDA(cudaMemcpyAsync(din, in_host, bytes, cudaMemcpyHostToDevice, s));
-    HopArgs a = hop_args(c, prec, out_parity, dout, din, nrhs);
-    PLQ_TRY(launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s));
-    PLQ_CUDA(cudaMemcpyAsync(out_host, dout, bytes, cudaMemcpyDeviceToHost, s));
-    PLQ_CUDA(cudaStreamSynchronize(s));
+    const char *hin = static_cast<const char *>(in_host);
+    char *hout = static_cast<char *>(out_host);
+    // Pipeline over time slabs, the overlap of Sec. 2.2 applied to the host
+    // link: input slabs stream in on one copy engine, the output sites whose
+    // neighbours (t - 1, t, t + 1) have all arrived are computed, and finished
+    // output slabs stream back on the other engine while later slabs compute.
+    const int T = c->lat.L[0];
+    const int slab = c->lat.Vh / T;  // checkerboard sites per time slice
+    const int K = T < 8 ? T : 8;
+    const size_t n = (size_t)nrhs, VhN = (size_t)c->lat.Vh * n;
+    const int nplanes = prec == PLQ_F64 ? 12 : prec == PLQ_F32 ? 6 : 3;
+    auto chunk_t0 = [&](int k) { return (int)((long long)T * k / K); };
+    auto copy_chunk = [&](char *dst, const char *src, int k, cudaMemcpyKind kind, cudaStream_t s) -> cudaError_t {
+        const size_t e0 = (size_t)chunk_t0(k) * slab * n, e1 = (size_t)chunk_t0(k + 1) * slab * n;
+        cudaError_t e = cudaMemcpy2DAsync(dst + e0 * 16, VhN * 16, src + e0 * 16, VhN * 16, (e1 - e0) * 16, nplanes,
+                                          kind, s);
+        if (e == cudaSuccess && prec == PLQ_F16)  // per-site norms
+            e = cudaMemcpyAsync(dst + 48 * VhN + e0 * 4, src + 48 * VhN + e0 * 4, (e1 - e0) * 4, kind, s);
+        return e;
+    };
+    cudaEvent_t *ev_in = c->ev, *ev_done = c->ev + 64, *ev_start = c->ev + 128;
+    PLQ_CUDA(cudaEventRecord(ev_start[0], user));
+    PLQ_CUDA(cudaStreamWaitEvent(c->copy_in, ev_start[0], 0));
+    PLQ_CUDA(cudaStreamWaitEvent(c->compute, ev_start[0], 0));
+    PLQ_CUDA(cudaStreamWaitEvent(c->copy_out, ev_start[0], 0));
+    // input order: the last slab first (slab 0 needs it through the periodic time direction)
+    for (int q = 0; q < K; ++q) {
+        const int k = (q + K - 1) % K;
+        PLQ_CUDA(copy_chunk(din, hin, k, cudaMemcpyHostToDevice, c->copy_in));
+        PLQ_CUDA(cudaEventRecord(ev_in[k], c->copy_in));
+    }
+    for (int k = 0; k < K; ++k) {
+        PLQ_CUDA(cudaStreamWaitEvent(c->compute, ev_in[(k + K - 1) % K], 0));
+        PLQ_CUDA(cudaStreamWaitEvent(c->compute, ev_in[k], 0));
+        PLQ_CUDA(cudaStreamWaitEvent(c->compute, ev_in[(k + 1) % K], 0));
+        HopArgs a = hop_args(c, prec, out_parity, dout, din, nrhs);
+        a.site_begin = chunk_t0(k) * slab;
+        a.site_end = chunk_t0(k + 1) * slab;
+        PLQ_TRY(launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, c->compute));
+        PLQ_CUDA(cudaEventRecord(ev_done[k], c->compute));
+        PLQ_CUDA(cudaStreamWaitEvent(c->copy_out, ev_done[k], 0));
+        PLQ_CUDA(copy_chunk(hout, dout, k, cudaMemcpyDeviceToHost, c->copy_out));
+    }
+    PLQ_CUDA(cudaEventRecord(ev_start[1], c->copy_out));
+    PLQ_CUDA(cudaStreamWaitEvent(user, ev_start[1], 0));
+    PLQ_CUDA(cudaStreamSynchronize(user));
     return PLQ_OK;
 }
 
@@ -307,6 +367,30 @@ plq_status plq_wilson_apply(plq_ctx *c, void *out, const void *in, double kappa,
     HopArgs b = hop_args(c, prec, 1, oo, ie);
     b.x = io;
     b.a = -kappa;
+    return launch_hop(b, prec, c->gauge[prec].reals, EPI_XPAY, s);
+}
+
+plq_status plq_twisted_apply(plq_ctx *c, void *out, const void *in, double kappa, double mu, int prec,
+                             void *stream) {
+    PLQ_TRY(check_ctx(c));
+    if (!aligned16(out) || !aligned16(in)) return set_error(PLQ_ERR_ARG, "null or misaligned field pointer");
+    if (out == in) return set_error(PLQ_ERR_ARG, "in and out must not overlap");
+    PLQ_TRY(need_gauge(c, prec));
+    PLQ_TRY(use_device(c));
+    const size_t half = plq_field_bytes(c, prec, 1);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const char *ie = static_cast<const char *>(in), *io = ie + half;
+    char *oe = static_cast<char *>(out), *oo = oe + half;
+    // out_p = (1 + 2 i kappa mu gamma5) in_p - kappa H_{p,1-p} in_{1-p}
+    HopArgs a = hop_args(c, prec, 0, oe, io);
+    a.x = ie;
+    a.a = -kappa;
+    a.nu_x = 2.0 * kappa * mu;
+    PLQ_TRY(launch_hop(a, prec, c->gauge[prec].reals, EPI_XPAY, s));
+    HopArgs b = hop_args(c, prec, 1, oo, ie);
+    b.x = io;
+    b.a = -kappa;
+    b.nu_x = 2.0 * kappa * mu;
     return launch_hop(b, prec, c->gauge[prec].reals, EPI_XPAY, s);
 }
 

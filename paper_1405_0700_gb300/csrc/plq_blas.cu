@@ -183,6 +183,22 @@ __global__ void accumulate_kernel(long long N, void *dst, const void *src) {
     }
 }
 
+// dst = scale (1 + i nu gamma5) src
+template <int P>
+__global__ void twist_kernel(long long N, void *dst, const void *src, double nu, double scale) {
+    using T = RealOf<P>;
+    ELEM_LOOP(N) {
+        cx<T> v[12];
+        Spinor<P>::load(src, N, e, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const T g = (T)(k < 6 ? nu : -nu);
+            v[k] = {(T)scale * (v[k].re - g * v[k].im), (T)scale * (v[k].im + g * v[k].re)};
+        }
+        Spinor<P>::store(dst, N, e, v);
+    }
+}
+
 // y = x + a y  (FP64)
 __global__ void xpay64_kernel(long long N, const void *x, double a, void *y) {
     ELEM_LOOP(N) {
@@ -350,6 +366,13 @@ plq_status blas_cg_direction(long long N, int n, void *p, const void *r, int pre
 plq_status blas_accumulate(long long N, void *dst64, const void *src, int ps, cudaStream_t s) {
     const int grid = grid_for(N, false);
     DISPATCH_P(ps, accumulate_kernel, N, dst64, src);
+    PLQ_CUDA(cudaGetLastError());
+    return PLQ_OK;
+}
+
+plq_status blas_twist(long long N, void *dst, const void *src, int prec, double nu, double scale, cudaStream_t s) {
+    const int grid = grid_for(N, false);
+    DISPATCH_P(prec, twist_kernel, N, dst, src, nu, scale);
     PLQ_CUDA(cudaGetLastError());
     return PLQ_OK;
 }

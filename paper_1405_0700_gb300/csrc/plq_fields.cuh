@@ -278,6 +278,9 @@ __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isf
 // Finalize step of one right-hand side's reduction: update its solver
 // scalars in device memory from the grid totals tot[0..NV).
 __device__ __forceinline__ void finalize_one(int fin, SolverState *st, const double *tot) {
+    // A frozen right-hand side contributed nothing to this reduction: its
+    // scalars must not change.
+    if (st->stop) return;
     switch (fin) {
     case FIN_CG_ALPHA:
         st->pAp = tot[0];
@@ -343,6 +346,10 @@ struct RedAcc {
     }
 };
 
+// Linear thread index and thread count of a (possibly 2-D) block.
+__device__ __forceinline__ int ltid() { return threadIdx.y * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int lsize() { return blockDim.x * blockDim.y; }
+
 // Must be called by every thread of the block before any add().
 template <int NV, class R>
 __device__ __forceinline__ void red_init(RedAcc<NV, R> &acc, int n) {
@@ -351,7 +358,7 @@ __device__ __forceinline__ void red_init(RedAcc<NV, R> &acc, int n) {
     acc.sm = slots;
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc.v[k] = R(0);
-    for (int t = threadIdx.x; t < NV * n; t += blockDim.x) slots[t] = R(0);
+    for (int t = ltid(); t < NV * n; t += lsize()) slots[t] = R(0);
     __syncthreads();
 }
 
@@ -360,48 +367,59 @@ __device__ __forceinline__ void red_init(RedAcc<NV, R> &acc, int n) {
 // adds them in block order -- deterministic -- stores the totals in
 // red.sums[k*n + r] and applies the finalize step to red.st[r].  Every thread
 // of every block must call it.
+// Sum over the lanes of a warp that may be partial (the block's thread count
+// need not be a multiple of 32); lane 0 gets the total.
+template <class V>
+__device__ __forceinline__ V warp_sum(V x, int lane, int active) {
+    const unsigned mask = active >= 32 ? 0xffffffffu : ((1u << active) - 1u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const V y = __shfl_down_sync(mask, x, o);
+        if (lane + o < active) x += y;
+    }
+    return x;
+}
+
 template <int NV, class R>
 __device__ void grid_reduce(const Reduce &red, RedAcc<NV, R> &acc) {
     __shared__ double wsum[32][NV];
     __shared__ double tots[kPartialSlots];
     __shared__ bool last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int tid = ltid(), lane = tid & 31, warp = tid >> 5, nthr = lsize(), nw = (nthr + 31) >> 5;
+    const int active = min(32, nthr - warp * 32);  // lanes present in this thread's warp
     const int n = acc.n, slots = NV * n;
     double *mine = red.partials + (size_t)blockIdx.x * kPartialSlots;
     if (n == 1) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            R x = acc.v[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            const R x = warp_sum(acc.v[k], lane, active);
             if (lane == 0) wsum[warp][k] = (double)x;
         }
         __syncthreads();
-        if (threadIdx.x < NV) {
+        if (tid < NV) {
             double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += wsum[w][threadIdx.x];
-            mine[threadIdx.x] = s;
+            for (int w = 0; w < nw; ++w) s += wsum[w][tid];
+            mine[tid] = s;
         }
     } else {
         __syncthreads();  // all shared-memory atomics of the block are done
-        for (int t = threadIdx.x; t < slots; t += blockDim.x) mine[t] = (double)acc.sm[t];
+        for (int t = tid; t < slots; t += nthr) mine[t] = (double)acc.sm[t];
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(red.ticket, 1u) == gridDim.x - 1);
+    if (tid == 0) last = (atomicAdd(red.ticket, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
     for (int t = warp; t < slots; t += nw) {
         double s = 0.0;
         for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(red.partials + (size_t)b * kPartialSlots + t);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        s = warp_sum(s, lane, active);
         if (lane == 0) tots[t] = s;
     }
     __syncthreads();
-    if (threadIdx.x < n) {
-        const int r = threadIdx.x;
+    if (tid < n) {
+        const int r = tid;
         double tr[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -410,7 +428,7 @@ __device__ void grid_reduce(const Reduce &red, RedAcc<NV, R> &acc) {
         }
         if (red.st) finalize_one(red.fin, red.st + r, tr);
     }
-    if (threadIdx.x == 0) *red.ticket = 0u;
+    if (tid == 0) *red.ticket = 0u;
 }
 
 // ---------------------------------------------------------------- geometry

@@ -1,0 +1,10 @@
+// Hopping-kernel instantiations for PLQ_F64 storage, 18-real links.
+#include "plq_hop_impl.cuh"
+
+namespace plq {
+
+plq_status launch_hop_f64_18(const HopArgs &a, int epi, cudaStream_t s, int block) {
+    return dispatch_hop<PLQ_F64, 18>(a, epi, s, block);
+}
+
+}  // namespace plq

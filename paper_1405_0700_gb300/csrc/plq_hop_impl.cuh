@@ -25,6 +25,16 @@
 
 namespace plq {
 
+// v = scale * (1 + i nu gamma5) v with gamma5 = diag(1, 1, -1, -1) in spin
+template <class T>
+__device__ __forceinline__ void twist12(cx<T> v[12], T nu, T scale) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const T g = k < 6 ? nu : -nu;
+        v[k] = {scale * (v[k].re - g * v[k].im), scale * (v[k].im + g * v[k].re)};
+    }
+}
+
 template <int MU>
 struct Proj;
 template <>
@@ -105,10 +115,13 @@ __device__ __forceinline__ int lex_stride(const Lattice &L, int mu) {
     return mu == 0 ? L.L[1] * L.L[2] * L.L[3] : mu == 1 ? 1 : mu == 2 ? L.L[1] : L.L[1] * L.L[2];
 }
 
-// Contribution of direction MU (forward and backward) to acc.
+// Contribution of direction MU (forward and backward) to the accumulators of
+// RT right-hand sides r0 .. r0+RT-1 of output site i.  Each link is loaded once
+// and applied to all RT neighbour spinors.
 // DAG: gamma5 H gamma5 = H^dagger, i.e. the projectors (1 -/+ gamma) swapped.
-template <int P, int R, int MU, bool DAG, bool TBL>
-__device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int i, int rr, cx<RealOf<P>> acc[12]) {
+template <int P, int R, int MU, bool DAG, bool TBL, int RT>
+__device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int i, int r0,
+                                        cx<RealOf<P>> (&acc)[RT][12]) {
     using T = RealOf<P>;
     const Lattice &L = a.lat;
     const int n = a.nrhs;
@@ -133,19 +146,22 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
             j = yl >> 1;
             flip = MU == 0 && cm == Lm - 1 && L.t_bc < 0;
         }
-        cx<T> phi[12];
-        Spinor<P>::load(a.in, stride, (size_t)j * n + rr, phi);
-        cx<T> h[6];
-        project<MU, SF>(phi, h);
-        if (MU == 0 && flip) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) h[k] = {-h[k].re, -h[k].im};
-        }
         cx<T> u[3][3];
         Link<P, R>::load(gbase + (size_t)(a.out_parity * 4 + MU) * a.gblock, L.Vh, i, u);
-        cx<T> uh[6];
-        su3_mul(u, h, uh);
-        reconstruct<MU, SF>(acc, uh);
+#pragma unroll
+        for (int t = 0; t < RT; ++t) {
+            cx<T> phi[12];
+            Spinor<P>::load(a.in, stride, (size_t)j * n + r0 + t, phi);
+            cx<T> h[6];
+            project<MU, SF>(phi, h);
+            if (MU == 0 && flip) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) h[k] = {-h[k].re, -h[k].im};
+            }
+            cx<T> uh[6];
+            su3_mul(u, h, uh);
+            reconstruct<MU, SF>(acc[t], uh);
+        }
     }
     // backward neighbour x - mu
     {
@@ -160,23 +176,36 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
             j = yl >> 1;
             flip = MU == 0 && cm == 0 && L.t_bc < 0;
         }
-        cx<T> phi[12];
-        Spinor<P>::load(a.in, stride, (size_t)j * n + rr, phi);
-        cx<T> h[6];
-        project<MU, SB>(phi, h);
-        if (MU == 0 && flip) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) h[k] = {-h[k].re, -h[k].im};
-        }
         cx<T> u[3][3];
         Link<P, R>::load(gbase + (size_t)((1 - a.out_parity) * 4 + MU) * a.gblock, L.Vh, j, u);
-        cx<T> uh[6];
-        su3_dag_mul(u, h, uh);
-        reconstruct<MU, SB>(acc, uh);
+#pragma unroll
+        for (int t = 0; t < RT; ++t) {
+            cx<T> phi[12];
+            Spinor<P>::load(a.in, stride, (size_t)j * n + r0 + t, phi);
+            cx<T> h[6];
+            project<MU, SB>(phi, h);
+            if (MU == 0 && flip) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) h[k] = {-h[k].re, -h[k].im};
+            }
+            cx<T> uh[6];
+            su3_dag_mul(u, h, uh);
+            reconstruct<MU, SB>(acc[t], uh);
+        }
     }
 }
 
-template <int P, int R, int EPI, bool DAG, bool TBL>
+// Single right-hand-side form (used by the batched persistent kernel).
+template <int P, int R, int MU, bool DAG, bool TBL>
+__device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int i, int rr, cx<RealOf<P>> acc[12]) {
+    cx<RealOf<P>>(&a1)[1][12] = *reinterpret_cast<cx<RealOf<P>>(*)[1][12]>(acc);
+    hop_dir<P, R, MU, DAG, TBL, 1>(a, g, i, rr, a1);
+}
+
+// Threads are arranged as (n / RT right-hand-side tiles) x (sites): the
+// threads of one site are adjacent and share its link loads through L1, and
+// each thread applies every link it loads to RT right-hand sides.
+template <int P, int R, int EPI, bool DAG, bool TBL, int RT = 1>
 __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
     using T = RealOf<P>;
     const int n = a.nrhs;
@@ -186,96 +215,142 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
     RedAcc<(NV > 0 ? NV : 1), T> racc;
     if constexpr (NV > 0) red_init(racc, n);
 
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int i = n == 1 ? (int)idx : (int)(idx / n);
-        const int rr = (int)(idx - (long long)i * n);
-        if (a.st != nullptr && a.st[rr].stop) continue;  // frozen right-hand side
+    const int r0 = threadIdx.x * RT;
+    const int i_end = a.site_end < 0 ? a.lat.Vh : a.site_end;
+    for (int i = a.site_begin + blockIdx.x * blockDim.y + threadIdx.y; i < i_end; i += gridDim.x * blockDim.y) {
+        bool all_frozen = a.st != nullptr;
+#pragma unroll
+        for (int t = 0; t < RT; ++t) all_frozen = all_frozen && a.st[r0 + t].stop;
+        if (all_frozen) continue;  // frozen right-hand sides
         SiteGeom g{};
         if constexpr (!TBL) g = site_geom(a.lat, a.out_parity, i);
-        cx<T> acc[12];
+        cx<T> acc[RT][12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k] = {T(0), T(0)};
-        hop_dir<P, R, 0, DAG, TBL>(a, g, i, rr, acc);
-        hop_dir<P, R, 1, DAG, TBL>(a, g, i, rr, acc);
-        hop_dir<P, R, 2, DAG, TBL>(a, g, i, rr, acc);
-        hop_dir<P, R, 3, DAG, TBL>(a, g, i, rr, acc);
+        for (int t = 0; t < RT; ++t)
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[t][k] = {T(0), T(0)};
+        hop_dir<P, R, 0, DAG, TBL, RT>(a, g, i, r0, acc);
+        hop_dir<P, R, 1, DAG, TBL, RT>(a, g, i, r0, acc);
+        hop_dir<P, R, 2, DAG, TBL, RT>(a, g, i, r0, acc);
+        hop_dir<P, R, 3, DAG, TBL, RT>(a, g, i, r0, acc);
 
-        if constexpr (EPI != EPI_PLAIN) {
-            cx<T> xv[12];
-            Spinor<P>::load(a.x, stride, (size_t)idx, xv);
-            const T s = (T)a.a;
 #pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                acc[k].re = fma(s, acc[k].re, xv[k].re);
-                acc[k].im = fma(s, acc[k].im, xv[k].im);
-            }
-            if constexpr (EPI == EPI_XPAY_NORM) {
-                T s0 = 0;
+        for (int t = 0; t < RT; ++t) {
+            const int rr = r0 + t;
+            if (RT > 1 && a.st != nullptr && a.st[rr].stop) continue;
+            const long long idx = (long long)i * n + rr;
+            if (a.nu_h != 0.0 || a.scale_h != 1.0) twist12(acc[t], (T)a.nu_h, (T)a.scale_h);
+            if constexpr (EPI != EPI_PLAIN) {
+                cx<T> xv[12];
+                Spinor<P>::load(a.x, stride, (size_t)idx, xv);
+                if (a.nu_x != 0.0) twist12(xv, (T)a.nu_x, T(1));
+                const T s = (T)a.a;
 #pragma unroll
-                for (int k = 0; k < 12; ++k) s0 += acc[k].re * acc[k].re + acc[k].im * acc[k].im;
-                racc.add(0, rr, s0);
-            } else if constexpr (EPI == EPI_XPAY_DOTW) {
-                cx<T> wv[12];
-                Spinor<P>::load(a.w, stride, (size_t)idx, wv);
-                T s0 = 0, s1 = 0;
-#pragma unroll
-                for (int k = 0; k < 12; ++k) {  // <w, out> = sum conj(w) out
-                    s0 += wv[k].re * acc[k].re + wv[k].im * acc[k].im;
-                    s1 += wv[k].re * acc[k].im - wv[k].im * acc[k].re;
+                for (int k = 0; k < 12; ++k) {
+                    acc[t][k].re = fma(s, acc[t][k].re, xv[k].re);
+                    acc[t][k].im = fma(s, acc[t][k].im, xv[k].im);
                 }
-                racc.add(0, rr, s0);
-                racc.add(1, rr, s1);
-            } else if constexpr (EPI == EPI_XPAY_TS) {
-                T s0 = 0, s1 = 0, s2 = 0;
+                if constexpr (EPI == EPI_XPAY_NORM) {
+                    T s0 = 0;
 #pragma unroll
-                for (int k = 0; k < 12; ++k) {  // <out, x> and |out|^2
-                    s0 += acc[k].re * xv[k].re + acc[k].im * xv[k].im;
-                    s1 += acc[k].re * xv[k].im - acc[k].im * xv[k].re;
-                    s2 += acc[k].re * acc[k].re + acc[k].im * acc[k].im;
+                    for (int k = 0; k < 12; ++k) s0 += acc[t][k].re * acc[t][k].re + acc[t][k].im * acc[t][k].im;
+                    racc.add(0, rr, s0);
+                } else if constexpr (EPI == EPI_XPAY_DOTW) {
+                    cx<T> wv[12];
+                    Spinor<P>::load(a.w, stride, (size_t)idx, wv);
+                    T s0 = 0, s1 = 0;
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) {  // <w, out> = sum conj(w) out
+                        s0 += wv[k].re * acc[t][k].re + wv[k].im * acc[t][k].im;
+                        s1 += wv[k].re * acc[t][k].im - wv[k].im * acc[t][k].re;
+                    }
+                    racc.add(0, rr, s0);
+                    racc.add(1, rr, s1);
+                } else if constexpr (EPI == EPI_XPAY_TS) {
+                    T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) {  // <out, x> and |out|^2
+                        s0 += acc[t][k].re * xv[k].re + acc[t][k].im * xv[k].im;
+                        s1 += acc[t][k].re * xv[k].im - acc[t][k].im * xv[k].re;
+                        s2 += acc[t][k].re * acc[t][k].re + acc[t][k].im * acc[t][k].im;
+                    }
+                    racc.add(0, rr, s0);
+                    racc.add(1, rr, s1);
+                    racc.add(2, rr, s2);
                 }
-                racc.add(0, rr, s0);
-                racc.add(1, rr, s1);
-                racc.add(2, rr, s2);
             }
+            Spinor<P>::store(a.out, stride, (size_t)idx, acc[t]);
         }
-        Spinor<P>::store(a.out, stride, (size_t)idx, acc);
     }
     if constexpr (NV > 0) grid_reduce(a.red, racc);
 }
 
 // Launch helper: grid = min(work blocks, resident blocks on all SMs).
-template <int P, int R, int EPI, bool DAG, bool TBL = false>
+template <int P, int R, int EPI, bool DAG, bool TBL = false, int RT = 1>
 plq_status launch_hop_t(const HopArgs &a, cudaStream_t s, int block) {
     if (a.block > 0) block = a.block;
-    static int per_sm[1025] = {0};
-    auto kern = hop_kernel<P, R, EPI, DAG, TBL>;
-    if (block <= 0 || block > 1024) block = 128;
-    if (per_sm[block] == 0) {
+    if (block <= 0 || block > 256) block = 128;
+    const int n = a.nrhs;
+    const int tiles = n / RT;  // threads per site
+    // sites per block: as many as fit in `block` threads, rounded so that the
+    // block is a whole number of warps when that is possible
+    int spb = block / tiles > 0 ? block / tiles : 1;
+    for (int q = spb; q >= 1; --q)
+        if ((q * tiles) % 32 == 0) {
+            spb = q;
+            break;
+        }
+    const int threads = tiles * spb;
+    static int per_sm[257] = {0};
+    auto kern = hop_kernel<P, R, EPI, DAG, TBL, RT>;
+    if (per_sm[threads] == 0) {
         int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, block, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0);
         if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(hop)");
-        per_sm[block] = nb > 0 ? nb : 1;
+        per_sm[threads] = nb > 0 ? nb : 1;
     }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long total = (long long)a.lat.Vh * a.nrhs;
-    long long want = (total + block - 1) / block;
-    long long cap = (long long)per_sm[block] * sms;
+    const int i_end = a.site_end < 0 ? a.lat.Vh : a.site_end;
+    long long want = ((long long)(i_end - a.site_begin) + spb - 1) / spb;
+    long long cap = (long long)per_sm[threads] * sms;
     if (EPI >= EPI_XPAY_NORM && cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
     const int grid = (int)(want < cap ? want : cap);
     if (grid <= 0) return PLQ_OK;
-    kern<<<grid, block, 0, s>>>(a);
+    const dim3 bdim(tiles, spb);
+    kern<<<grid, bdim, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "hop_kernel launch");
     return PLQ_OK;
 }
 
+template <int P, int R, int RT>
+plq_status dispatch_tiled(const HopArgs &a, int epi, cudaStream_t s, int block) {
+    switch (epi) {
+    case EPI_PLAIN:
+        return a.dagger ? launch_hop_t<P, R, EPI_PLAIN, true, false, RT>(a, s, block)
+                        : launch_hop_t<P, R, EPI_PLAIN, false, false, RT>(a, s, block);
+    case EPI_XPAY:
+        return a.dagger ? launch_hop_t<P, R, EPI_XPAY, true, false, RT>(a, s, block)
+                        : launch_hop_t<P, R, EPI_XPAY, false, false, RT>(a, s, block);
+    default:
+        return a.dagger ? launch_hop_t<P, R, EPI_XPAY_NORM, true, false, RT>(a, s, block)
+                        : launch_hop_t<P, R, EPI_XPAY_NORM, false, false, RT>(a, s, block);
+    }
+}
+
 template <int P, int R>
 plq_status dispatch_hop(const HopArgs &a, int epi, cudaStream_t s, int block) {
-    // The neighbour-table variants exist for the plain and xpay epilogues
-    // (operator applications); the reducing epilogues compute indices inline.
+    // Right-hand-side tiles (RT > 1) exist for the FP32-arithmetic storage
+    // formats and the epilogues of operator applications and CG; the
+    // neighbour-table variants for the plain and xpay epilogues.
+    if constexpr (P != PLQ_F64) {
+        if (a.rhs_tile > 1 && a.nrhs % a.rhs_tile == 0 && epi <= EPI_XPAY_NORM) {
+            if (a.rhs_tile == 2) return dispatch_tiled<P, R, 2>(a, epi, s, block);
+            if (a.rhs_tile == 4) return dispatch_tiled<P, R, 4>(a, epi, s, block);
+        }
+    }
     const bool tbl = a.nbr != nullptr;
     switch (epi) {
     case EPI_PLAIN:

@@ -101,6 +101,7 @@ constexpr int kPartialSlots = 64;  // >= 4 values x PLQ_MAX_RHS right-hand sides
 struct TuneEntry {
     int block = 0;       // 0 = default
     int index_mode = 0;  // 0 inline coordinates, 1 neighbour table
+    int rhs_tile = 1;    // right-hand sides per thread
     float us = 0.f;
 };
 
@@ -123,12 +124,15 @@ struct Ctx {
     // staging for the host entry points
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr, compute = nullptr;  // host-path pipeline
+    cudaEvent_t ev[3 * 64] = {};
     int num_sms = 0;
 };
 
 plq_status ensure_work(Ctx *c, size_t bytes);
 plq_status ensure_nbr_tables(Ctx *c);
 plq_status ensure_stage(Ctx *c, size_t bytes);
+plq_status ensure_pipeline(Ctx *c);
 
 // ---------------------------------------------------------------- hopping
 enum Epilogue {
@@ -159,6 +163,13 @@ struct HopArgs {
     // neighbours are computed from the coordinates.
     const int *nbr = nullptr;
     int block = 0;  // threads per block; 0 = default
+    int rhs_tile = 1;  // right-hand sides per thread (1, 2 or 4; must divide nrhs)
+    // Twisted-mass epilogue terms (0 = plain Wilson): the hopping result is
+    // replaced by scale_h * (1 + i nu_h gamma5) H in, and the xpay source x by
+    // (1 + i nu_x gamma5) x.
+    double nu_x = 0.0, nu_h = 0.0, scale_h = 1.0;
+    int site_begin = 0;   // output sites [site_begin, site_end) of the parity;
+    int site_end = -1;    // -1: up to Vh
 };
 
 // Launch the hopping kernel for (prec, link reals, epilogue).  block = 0 picks
@@ -195,6 +206,8 @@ plq_status blas_cg_direction(long long N, int n, void *p, const void *r, int pre
                              cudaStream_t s);
 // dst(F64) += convert(src)
 plq_status blas_accumulate(long long N, void *dst64, const void *src, int psrc, cudaStream_t s);
+// dst = scale * (1 + i nu gamma5) src (same precision, may alias)
+plq_status blas_twist(long long N, void *dst, const void *src, int prec, double nu, double scale, cudaStream_t s);
 // y = x + a * y (FP64, host scalar)
 plq_status blas_xpay64(long long N, const void *x, double a, void *y, cudaStream_t s);
 // BiCGstab: p = r + beta (p - omega v); s = r - alpha v; x += alpha p + omega s, r = s - omega t, <rhat, r>, |r|^2

@@ -49,7 +49,13 @@ struct Solve {
     double kappa;
     int P;   // inner storage precision
     int PX;  // inner solution accumulator precision
+    double nu = 0.0;  // twisted mass: nu = 2 kappa mu (0 = Wilson)
     double hops = 0;
+};
+
+// Twisted-mass terms of one hopping launch (all zero / one for Wilson).
+struct Tw {
+    double nu_x = 0.0, nu_h = 0.0, scale_h = 1.0;
 };
 
 Reduce reduce_of(plq_ctx *c, int fin) {
@@ -63,7 +69,7 @@ Reduce reduce_of(plq_ctx *c, int fin) {
 }
 
 plq_status hop(Solve &S, int prec, int out_par, void *out, const void *in, int epi, int dagger, const void *x,
-               double a, int fin = FIN_NONE, const void *w = nullptr, bool freeze = false) {
+               double a, int fin = FIN_NONE, const void *w = nullptr, bool freeze = false, Tw tw = Tw()) {
     plq_ctx *c = S.c;
     HopArgs h;
     h.in = in;
@@ -80,9 +86,31 @@ plq_status hop(Solve &S, int prec, int out_par, void *out, const void *in, int e
     h.red = reduce_of(c, fin);
     if (fin == FIN_NONE) h.red.st = nullptr;
     h.st = freeze ? c->state : nullptr;
+    h.nu_x = tw.nu_x;
+    h.nu_h = tw.nu_h;
+    h.scale_h = tw.scale_h;
     apply_tune(c, prec, S.n, h);
     S.hops += 1;
     return launch_hop(h, prec, c->gauge[prec].reals, epi, S.s);
+}
+
+// The two half-applications of Mhat (dagger: Mhat^dagger = gamma5 Mhat(-mu) gamma5):
+//   Mhat v = A v - kappa^2 H_eo A^{-1} H_oe v,  A = 1 + i nu gamma5.
+Tw tw_first(const Solve &S, bool dag) {  // A^{-1} (or A(-mu)^{-1}) on H_oe v
+    Tw t;
+    t.nu_h = dag ? S.nu : -S.nu;
+    t.scale_h = 1.0 / (1.0 + S.nu * S.nu);
+    return t;
+}
+Tw tw_second(const Solve &S, bool dag) {  // A (or A(-mu)) on the source
+    Tw t;
+    t.nu_x = dag ? -S.nu : S.nu;
+    return t;
+}
+Tw tw_diag(const Solve &S) {  // A on the xpay source of a full M application
+    Tw t;
+    t.nu_x = S.nu;
+    return t;
 }
 
 plq_status read_sums(Solve &S, double *out, int count) {
@@ -171,6 +199,7 @@ struct Params {
     double delta;
     int use_x0;
     int k;
+    double mu;
 };
 
 plq_status parse(const plq_solver_params *p, Params *o) {
@@ -180,6 +209,8 @@ plq_status parse(const plq_solver_params *p, Params *o) {
     o->delta = (p && p->delta > 0) ? p->delta : 0.1;
     o->use_x0 = p ? p->use_x0 : 0;
     o->k = (p && p->check_every > 0) ? p->check_every : 16;
+    o->mu = p ? p->mu : 0.0;
+    if (!std::isfinite(o->mu)) return set_error(PLQ_ERR_ARG, "twisted mass mu not finite");
     if (!valid_prec(o->inner)) return set_error(PLQ_ERR_ARG, "bad inner precision %d", o->inner);
     if (o->delta >= 1.0) return set_error(PLQ_ERR_ARG, "delta must be < 1");
     if (o->k > 256) o->k = 256;
@@ -188,9 +219,10 @@ plq_status parse(const plq_solver_params *p, Params *o) {
 
 // s = bhat - Mhat x_e (FP64); per right-hand side |s|^2
 plq_status true_residual(Solve &S, void *s64, void *tmp_o64, const void *bhat, const void *xe, double *s2) {
-    PLQ_TRY(hop(S, PLQ_F64, 1, tmp_o64, xe, EPI_PLAIN, 0, nullptr, 0.0));
-    PLQ_TRY(blas_copy_convert(S.N, s64, PLQ_F64, xe, PLQ_F64, S.s));
-    PLQ_TRY(blas_xpay64(S.N, bhat, -1.0, s64, S.s));  // s = bhat - x_e
+    PLQ_TRY(hop(S, PLQ_F64, 1, tmp_o64, xe, EPI_PLAIN, 0, nullptr, 0.0, FIN_NONE, nullptr, false, tw_first(S, false)));
+    if (S.nu != 0.0) PLQ_TRY(blas_twist(S.N, s64, xe, PLQ_F64, S.nu, 1.0, S.s));  // s = A x_e
+    else PLQ_TRY(blas_copy_convert(S.N, s64, PLQ_F64, xe, PLQ_F64, S.s));
+    PLQ_TRY(blas_xpay64(S.N, bhat, -1.0, s64, S.s));  // s = bhat - A x_e
     PLQ_TRY(hop(S, PLQ_F64, 0, s64, tmp_o64, EPI_XPAY_NORM, 0, s64, S.kappa * S.kappa));
     return read_sums(S, s2, S.n);
 }
@@ -227,6 +259,7 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
     S.kappa = kappa;
     S.P = P.inner;
     S.PX = P.inner == PLQ_F64 ? PLQ_F64 : PLQ_F32;
+    S.nu = 2.0 * kappa * P.mu;
     const size_t h64 = spinor_site_bytes(PLQ_F64) * (size_t)S.N;
     const size_t hL = spinor_site_bytes(S.P) * (size_t)S.N;
     const size_t hX = spinor_site_bytes(S.PX) * (size_t)S.N;
@@ -292,8 +325,13 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
                 }
             }
         }
-        // bhat = b_e + kappa H_eo b_o
-        if ((st = hop(S, PLQ_F64, 0, bhat, bo, EPI_XPAY, 0, be, kappa)) != PLQ_OK) break;
+        // bhat = b_e + kappa H_eo A^{-1} b_o (A = 1 for Wilson)
+        const void *bsrc = bo;
+        if (S.nu != 0.0) {
+            if ((st = blas_twist(S.N, tmp_o64, bo, PLQ_F64, -S.nu, 1.0 / (1.0 + S.nu * S.nu), s)) != PLQ_OK) break;
+            bsrc = tmp_o64;
+        }
+        if ((st = hop(S, PLQ_F64, 0, bhat, bsrc, EPI_XPAY, 0, be, kappa)) != PLQ_OK) break;
 
         const double delta = S.P == PLQ_F64 ? 0.0 : P.delta;
         for (;;) {
@@ -338,8 +376,12 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
             }
             if (method == SOLVER_CG) {
                 // r = Mhat^dag s, the residual of the normal equations
-                if ((st = hop(S, PLQ_F64, 1, tmp_o64, s64, EPI_PLAIN, 1, nullptr, 0.0)) != PLQ_OK) break;
-                if ((st = hop(S, PLQ_F64, 0, r64, tmp_o64, EPI_XPAY_NORM, 1, s64, -kappa * kappa)) != PLQ_OK) break;
+                if ((st = hop(S, PLQ_F64, 1, tmp_o64, s64, EPI_PLAIN, 1, nullptr, 0.0, FIN_NONE, nullptr, false,
+                              tw_first(S, true))) != PLQ_OK)
+                    break;
+                if ((st = hop(S, PLQ_F64, 0, r64, tmp_o64, EPI_XPAY_NORM, 1, s64, -kappa * kappa, FIN_NONE, nullptr,
+                              false, tw_second(S, true))) != PLQ_OK)
+                    break;
                 if ((st = read_sums(S, r2.data(), n)) != PLQ_OK) break;
                 void *rL = L[0], *pL = L[1], *qL = L[2], *mpL = L[3], *toL = L[4];
                 if ((st = blas_copy_convert(S.N, rL, S.P, r64, PLQ_F64, s)) != PLQ_OK) break;
@@ -363,10 +405,11 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
                 const double kk = kappa * kappa;
                 const int PI = S.P;
                 auto body = [&]() -> plq_status {
-                    PLQ_TRY(hop(S, PI, 1, toL, pL, EPI_PLAIN, 0, nullptr, 0.0, FIN_NONE, nullptr, true));
-                    PLQ_TRY(hop(S, PI, 0, mpL, toL, EPI_XPAY_NORM, 0, pL, -kk, FIN_CG_ALPHA, nullptr, true));
-                    PLQ_TRY(hop(S, PI, 1, toL, mpL, EPI_PLAIN, 1, nullptr, 0.0, FIN_NONE, nullptr, true));
-                    PLQ_TRY(hop(S, PI, 0, qL, toL, EPI_XPAY, 1, mpL, -kk, FIN_NONE, nullptr, true));
+                    PLQ_TRY(hop(S, PI, 1, toL, pL, EPI_PLAIN, 0, nullptr, 0.0, FIN_NONE, nullptr, true, tw_first(S, false)));
+                    PLQ_TRY(hop(S, PI, 0, mpL, toL, EPI_XPAY_NORM, 0, pL, -kk, FIN_CG_ALPHA, nullptr, true,
+                                tw_second(S, false)));
+                    PLQ_TRY(hop(S, PI, 1, toL, mpL, EPI_PLAIN, 1, nullptr, 0.0, FIN_NONE, nullptr, true, tw_first(S, true)));
+                    PLQ_TRY(hop(S, PI, 0, qL, toL, EPI_XPAY, 1, mpL, -kk, FIN_NONE, nullptr, true, tw_second(S, true)));
                     Reduce rb = reduce_of(c, FIN_CG_BETA);
                     PLQ_TRY(blas_cg_update(S.N, n, xL, rL, pL, qL, PI, rb, c->state, s));
                     return blas_cg_direction(S.N, n, pL, rL, PI, c->state, s);
@@ -389,11 +432,13 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
                 const double kk = kappa * kappa;
                 const int PI = S.P;
                 auto body = [&]() -> plq_status {
-                    PLQ_TRY(hop(S, PI, 1, toL, pL, EPI_PLAIN, 0, nullptr, 0.0, FIN_NONE, nullptr, true));
-                    PLQ_TRY(hop(S, PI, 0, vL, toL, EPI_XPAY_DOTW, 0, pL, -kk, FIN_BICG_ALPHA, rhL, true));
+                    PLQ_TRY(hop(S, PI, 1, toL, pL, EPI_PLAIN, 0, nullptr, 0.0, FIN_NONE, nullptr, true, tw_first(S, false)));
+                    PLQ_TRY(hop(S, PI, 0, vL, toL, EPI_XPAY_DOTW, 0, pL, -kk, FIN_BICG_ALPHA, rhL, true,
+                                tw_second(S, false)));
                     PLQ_TRY(blas_bicg_s(S.N, n, sL, rL, vL, PI, c->state, s));
-                    PLQ_TRY(hop(S, PI, 1, toL, sL, EPI_PLAIN, 0, nullptr, 0.0, FIN_NONE, nullptr, true));
-                    PLQ_TRY(hop(S, PI, 0, tL, toL, EPI_XPAY_TS, 0, sL, -kk, FIN_BICG_OMEGA, nullptr, true));
+                    PLQ_TRY(hop(S, PI, 1, toL, sL, EPI_PLAIN, 0, nullptr, 0.0, FIN_NONE, nullptr, true, tw_first(S, false)));
+                    PLQ_TRY(hop(S, PI, 0, tL, toL, EPI_XPAY_TS, 0, sL, -kk, FIN_BICG_OMEGA, nullptr, true,
+                                tw_second(S, false)));
                     Reduce rb = reduce_of(c, FIN_BICG_RHO);
                     PLQ_TRY(blas_bicg_update(S.N, n, xL, rL, pL, sL, tL, rhL, PI, rb, c->state, s));
                     return blas_bicg_p(S.N, n, pL, rL, vL, PI, c->state, s);
@@ -426,14 +471,19 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
             first = false;
         }
         if (st != PLQ_OK) break;
-        // x_o = b_o + kappa H_oe x_e
+        // x_o = A^{-1} (b_o + kappa H_oe x_e)
         if ((st = hop(S, PLQ_F64, 1, xo, xe, EPI_XPAY, 0, bo, kappa)) != PLQ_OK) break;
+        if (S.nu != 0.0 && (st = blas_twist(S.N, xo, xo, PLQ_F64, -S.nu, 1.0 / (1.0 + S.nu * S.nu), s)) != PLQ_OK)
+            break;
         // full true residual ||b - M x|| with the FP64 operator, both parities
         std::vector<double> re(n), ro(n);
-        if ((st = hop(S, PLQ_F64, 0, t64, xo, EPI_XPAY, 0, xe, -kappa)) != PLQ_OK) break;
+        if ((st = hop(S, PLQ_F64, 0, t64, xo, EPI_XPAY, 0, xe, -kappa, FIN_NONE, nullptr, false, tw_diag(S))) != PLQ_OK)
+            break;
         if ((st = blas_xpay64(S.N, be, -1.0, t64, s)) != PLQ_OK) break;
         if ((st = norm2_64(S, t64, re.data())) != PLQ_OK) break;
-        if ((st = hop(S, PLQ_F64, 1, tmp_o64, xe, EPI_XPAY, 0, xo, -kappa)) != PLQ_OK) break;
+        if ((st = hop(S, PLQ_F64, 1, tmp_o64, xe, EPI_XPAY, 0, xo, -kappa, FIN_NONE, nullptr, false, tw_diag(S))) !=
+            PLQ_OK)
+            break;
         if ((st = blas_xpay64(S.N, bo, -1.0, tmp_o64, s)) != PLQ_OK) break;
         if ((st = norm2_64(S, tmp_o64, ro.data())) != PLQ_OK) break;
         for (int r = 0; r < n; ++r) {
@@ -476,6 +526,37 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
 }
 
 }  // namespace
+
+// ||b - M x||^2 and ||b||^2 of full FP64 fields with the FP64 operator (uses
+// the context's workspace; synchronises the stream).
+plq_status wilson_residual64(plq_ctx *c, double kappa, const void *x, const void *b, double *r2, double *b2,
+                             cudaStream_t s) {
+    Solve S;
+    S.c = c;
+    S.s = s;
+    S.Vh = c->lat.Vh;
+    S.n = 1;
+    S.N = S.Vh;
+    S.kappa = kappa;
+    const size_t h64 = spinor_site_bytes(PLQ_F64) * (size_t)S.Vh;
+    PLQ_TRY(ensure_work(c, 2 * h64));
+    char *te = static_cast<char *>(c->work), *to = te + h64;
+    const char *xe = static_cast<const char *>(x), *xo = xe + h64;
+    const char *be = static_cast<const char *>(b), *bo = be + h64;
+    double re = 0, ro = 0, ne = 0, no = 0;
+    PLQ_TRY(hop(S, PLQ_F64, 0, te, xo, EPI_XPAY, 0, xe, -kappa));
+    PLQ_TRY(blas_xpay64(S.N, be, -1.0, te, s));
+    PLQ_TRY(norm2_64(S, te, &re));
+    PLQ_TRY(hop(S, PLQ_F64, 1, to, xe, EPI_XPAY, 0, xo, -kappa));
+    PLQ_TRY(blas_xpay64(S.N, bo, -1.0, to, s));
+    PLQ_TRY(norm2_64(S, to, &ro));
+    PLQ_TRY(norm2_64(S, be, &ne));
+    PLQ_TRY(norm2_64(S, bo, &no));
+    *r2 = re + ro;
+    *b2 = ne + no;
+    return PLQ_OK;
+}
+
 }  // namespace plq
 
 extern "C" {

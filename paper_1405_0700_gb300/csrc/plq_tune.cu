@@ -49,11 +49,12 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         char k[600];
-        int block = 0, mode = 0;
+        int block = 0, mode = 0, tile = 1;
         float us = 0;
-        if (sscanf(line, "%599s %d %d %f", k, &block, &mode, &us) == 4 && key == k) {
+        if (sscanf(line, "%599s %d %d %d %f", k, &block, &mode, &tile, &us) == 5 && key == k) {
             e->block = block;
             e->index_mode = mode;
+            e->rhs_tile = tile;
             e->us = us;
             found = true;  // last entry wins
         }
@@ -65,7 +66,7 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
 void cache_store(const char *path, const std::string &key, const TuneEntry &e) {
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %.3f\n", key.c_str(), e.block, e.index_mode, e.us);
+    fprintf(f, "%s %d %d %d %.3f\n", key.c_str(), e.block, e.index_mode, e.rhs_tile, e.us);
     fclose(f);
 }
 
@@ -88,6 +89,7 @@ void apply_tune(const Ctx *c, int prec, int nrhs, HopArgs &a) {
     const TuneEntry &e = c->tune[prec][nrhs];
     if (e.block > 0) a.block = e.block;
     a.nbr = (e.index_mode == 1) ? c->nbr[a.out_parity] : nullptr;
+    a.rhs_tile = (e.rhs_tile > 1 && nrhs % e.rhs_tile == 0) ? e.rhs_tile : 1;
 }
 
 }  // namespace plq
@@ -110,6 +112,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
         if (res) {
             res->block = best.block;
             res->index_mode = best.index_mode;
+            res->rhs_tile = best.rhs_tile;
             res->us_per_launch = best.us;
             res->from_cache = 1;
         }
@@ -135,7 +138,18 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
     best.us = 1e30f;
     int tried = 0;
     const int reps = 10;
-    for (int mode = 0; mode < 2 && st == PLQ_OK; ++mode) {
+    // candidates: index mode x block size, plus right-hand-side tiles for nrhs > 1
+    struct Cand {
+        int mode, tile;
+    };
+    Cand cands[8];
+    int nc = 0;
+    cands[nc++] = {0, 1};
+    cands[nc++] = {1, 1};
+    if (prec != PLQ_F64 && nrhs % 2 == 0) cands[nc++] = {0, 2};
+    if (prec != PLQ_F64 && nrhs % 4 == 0) cands[nc++] = {0, 4};
+    for (int ci = 0; ci < nc && st == PLQ_OK; ++ci) {
+        const int mode = cands[ci].mode;
         for (int b : blocks) {
             HopArgs a;
             a.in = in;
@@ -147,6 +161,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
             a.lat = c->lat;
             a.block = b;
             a.nbr = mode ? c->nbr[0] : nullptr;
+            a.rhs_tile = cands[ci].tile;
             for (int w = 0; w < 2 && st == PLQ_OK; ++w) st = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
             cudaEventRecord(e0, s);
             for (int r = 0; r < reps && st == PLQ_OK; ++r) st = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
@@ -165,6 +180,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
                 best.us = us;
                 best.block = b;
                 best.index_mode = mode;
+                best.rhs_tile = cands[ci].tile;
             }
         }
     }
@@ -179,6 +195,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
     if (res) {
         res->block = best.block;
         res->index_mode = best.index_mode;
+        res->rhs_tile = best.rhs_tile;
         res->us_per_launch = best.us;
         res->from_cache = 0;
         res->candidates = tried;
@@ -186,16 +203,19 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
     return PLQ_OK;
 }
 
-extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, int index_mode) {
+extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, int index_mode, int rhs_tile) {
     if (!c) return set_error(PLQ_ERR_ARG, "null context");
     if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
     if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
     if (block != 0 && (block < 32 || block > 256 || (block % 32)))
         return set_error(PLQ_ERR_ARG, "block must be 0 or a multiple of 32 in 32..256");
     if (index_mode != 0 && index_mode != 1) return set_error(PLQ_ERR_ARG, "index_mode must be 0 or 1");
+    if (rhs_tile != 1 && rhs_tile != 2 && rhs_tile != 4) return set_error(PLQ_ERR_ARG, "rhs_tile must be 1, 2 or 4");
+    if (nrhs % rhs_tile) return set_error(PLQ_ERR_ARG, "rhs_tile must divide nrhs");
     PLQ_CUDA(cudaSetDevice(c->device));
     if (index_mode == 1) PLQ_TRY(ensure_nbr_tables(c));
     c->tune[prec][nrhs].block = block;
     c->tune[prec][nrhs].index_mode = index_mode;
+    c->tune[prec][nrhs].rhs_tile = rhs_tile;
     return PLQ_OK;
 }

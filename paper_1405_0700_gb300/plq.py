@@ -44,6 +44,7 @@ class SolverParams(ctypes.Structure):
         ("delta", ctypes.c_double),
         ("use_x0", ctypes.c_int),
         ("check_every", ctypes.c_int),
+        ("mu", ctypes.c_double),
     ]
 
 
@@ -51,9 +52,23 @@ class TuneResult(ctypes.Structure):
     _fields_ = [
         ("block", ctypes.c_int),
         ("index_mode", ctypes.c_int),
+        ("rhs_tile", ctypes.c_int),
         ("us_per_launch", ctypes.c_double),
         ("from_cache", ctypes.c_int),
         ("candidates", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("grid", ctypes.c_int),
+        ("block", ctypes.c_int),
+        ("graph_captured", ctypes.c_int),
+        ("launches", ctypes.c_int),
+        ("seconds", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -87,6 +102,7 @@ SIGNATURES = {
     "plq_hopping_eo": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _c_int, _vp]),
     "plq_hopping_eo_host": (_c_int, [_vp, _c_int, _vp, _vp, _c_int, _c_int, _vp]),
     "plq_wilson_apply": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, _vp]),
+    "plq_twisted_apply": (_c_int, [_vp, _vp, _vp, _c_double, _c_double, _c_int, _vp]),
     "plq_schur_apply": (_c_int, [_vp, _vp, _vp, _vp, _c_double, _c_int, _c_int, _vp]),
     "plq_cg_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo), _vp]),
     "plq_bicgstab_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams),
@@ -95,10 +111,13 @@ SIGNATURES = {
                                     ctypes.POINTER(SolveInfo), _vp]),
     "plq_bicgstab_solve_multi": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, ctypes.POINTER(SolverParams),
                                           ctypes.POINTER(SolveInfo), _vp]),
+    "plq_cg_solve_batched": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolverParams),
+                                      ctypes.POINTER(SolveInfo), ctypes.POINTER(BatchInfo), _vp]),
     "plq_measure_fma_rate": (_c_int, [_c_int, _c_int, ctypes.POINTER(ctypes.c_double)]),
     "plq_schur_apply_noalloc": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, _c_int, _vp]),
     "plq_autotune": (_c_int, [_vp, _c_int, _c_int, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
-    "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int]),
+    "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int]),
 }
 
 _lib = None
@@ -270,6 +289,11 @@ class Context:
         check(lib().plq_wilson_apply(self._h, _ptr(out), _ptr(inp), float(kappa), prec_of(prec), _stream(stream)))
         return out
 
+    def twisted_apply(self, out, inp, kappa, mu, prec, stream=None):
+        check(lib().plq_twisted_apply(self._h, _ptr(out), _ptr(inp), float(kappa), float(mu), prec_of(prec),
+                                      _stream(stream)))
+        return out
+
     def schur_apply(self, out, inp, tmp, kappa, prec, dagger=False, stream=None):
         check(lib().plq_schur_apply(self._h, _ptr(out), _ptr(inp), _ptr(tmp), float(kappa), int(bool(dagger)),
                                     prec_of(prec), _stream(stream)))
@@ -290,12 +314,13 @@ class Context:
         check(lib().plq_autotune(self._h, prec_of(prec), nrhs, path, ctypes.byref(r)))
         return r.as_dict()
 
-    def set_launch(self, prec, nrhs=1, block=0, index_mode=0):
-        check(lib().plq_set_launch(self._h, prec_of(prec), nrhs, block, index_mode))
+    def set_launch(self, prec, nrhs=1, block=0, index_mode=0, rhs_tile=1):
+        check(lib().plq_set_launch(self._h, prec_of(prec), nrhs, block, index_mode, rhs_tile))
 
     # ------------------------------------------------------------ solvers
-    def _solve(self, fn, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every, stream, raise_on_error):
-        p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every)
+    def _solve(self, fn, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every, stream, raise_on_error,
+               mu=0.0):
+        p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every, mu)
         info = SolveInfo()
         st = fn(self._h, _ptr(x), _ptr(b), float(kappa), ctypes.byref(p), ctypes.byref(info), _stream(stream))
         if raise_on_error:
@@ -303,14 +328,14 @@ class Context:
         return info
 
     def cg_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
-                 check_every=16, stream=None, raise_on_error=True):
-        """CG on the even-odd normal equations; x, b packed full FP64 fields."""
+                 check_every=16, stream=None, raise_on_error=True, mu=0.0):
+        """CG on the even-odd normal equations; x, b packed full FP64 fields (mu: twisted mass)."""
         return self._solve(lib().plq_cg_solve, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every,
-                           stream, raise_on_error)
+                           stream, raise_on_error, mu)
 
     def _solve_multi(self, fn, x, b, kappa, nrhs, tol, maxit, inner_prec, delta, use_x0, check_every, stream,
                      raise_on_error):
-        p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every)
+        p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every, 0.0)
         infos = (SolveInfo * nrhs)()
         st = fn(self._h, _ptr(x), _ptr(b), float(kappa), nrhs, ctypes.byref(p), infos, _stream(stream))
         if raise_on_error:
@@ -329,10 +354,27 @@ class Context:
                                  use_x0, check_every, stream, raise_on_error)
 
     def bicgstab_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
-                       check_every=16, stream=None, raise_on_error=True):
-        """BiCGstab on the even-odd Schur system; x, b packed full FP64 fields."""
+                       check_every=16, stream=None, raise_on_error=True, mu=0.0):
+        """BiCGstab on the even-odd Schur system; x, b packed full FP64 fields (mu: twisted mass)."""
         return self._solve(lib().plq_bicgstab_solve, x, b, kappa, tol, maxit, inner_prec, delta, use_x0,
-                           check_every, stream, raise_on_error)
+                           check_every, stream, raise_on_error, mu)
+
+
+def cg_solve_batched(ctxs, xs, bs, kappas, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
+                     stream=None, raise_on_error=True):
+    """One persistent launch solving len(ctxs) independent systems (see plq_cg_solve_batched)."""
+    n = len(ctxs)
+    H = (_vp * n)(*[c.handle.value for c in ctxs])
+    X = (_vp * n)(*[_ptr(x) for x in xs])
+    B = (_vp * n)(*[_ptr(b) for b in bs])
+    K = (ctypes.c_double * n)(*[float(k) for k in kappas])
+    p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), 16, 0.0)
+    infos = (SolveInfo * n)()
+    bi = BatchInfo()
+    st = lib().plq_cg_solve_batched(H, n, X, B, K, ctypes.byref(p), infos, ctypes.byref(bi), _stream(stream))
+    if raise_on_error:
+        check(st, (list(infos), bi))
+    return list(infos), bi.as_dict()
 
 
 def measure_fma_rate(prec, device=0):

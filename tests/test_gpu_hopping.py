@@ -116,6 +116,23 @@ def test_multi_rhs(nrhs, prec, reals):
         assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
 
 
+@pytest.mark.parametrize("tile", [2, 4])
+@pytest.mark.parametrize("prec,reals", [(F32, 18), (F32, 12), (F16, 12), (F16, 18)])
+def test_multi_rhs_tiles(tile, prec, reals):
+    # each thread applies every link it loads to `tile` right-hand sides
+    dims = (6, 4, 2, 4)
+    nrhs = 12
+    U = S.gauge_field(dims, 0.3, 16)
+    phis = np.stack([S.gaussian_spinor(dims, 200 + r) for r in range(nrhs)])
+    kappa = 0.11
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, reals, prec)
+        ctx.set_launch(prec, nrhs, 96, 0, tile)
+        got = gpu_hopping_full(ctx, phis, prec, nrhs).reshape(phis.shape)
+    for r in range(nrhs):
+        assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
+
+
 def test_host_entry_point_matches_device():
     dims = (8, 4, 4, 4)
     U, phi = S.gauge_and_spinor(dims, 0.3, 7)

@@ -125,7 +125,7 @@ def test_missing_inner_gauge_copy():
         assert e.value.status == plq.PLQ_ERR_STATE
 
 
-def run_multi(method, dims, eps, seed, kappa, inner, sources, **kw):
+def run_multi(method, dims, eps, seed, kappa, inner, sources, tile=1, **kw):
     U = S.gauge_field(dims, eps, seed)
     n = len(sources)
     b = np.stack(sources)
@@ -133,6 +133,7 @@ def run_multi(method, dims, eps, seed, kappa, inner, sources, **kw):
         ctx.gauge_upload(U, 18, F64)
         if inner != F64:
             ctx.gauge_upload(U, 12, inner)
+            ctx.set_launch(inner, n, 0, 0, tile)
         bd = ctx.to_device(b, F64, n)
         x = ctx.empty_full(F64, n)
         fn = ctx.cg_solve_multi if method == "cg" else ctx.bicgstab_solve_multi
@@ -144,6 +145,8 @@ def run_multi(method, dims, eps, seed, kappa, inner, sources, **kw):
 @pytest.mark.parametrize("method", ["cg", "bicgstab"])
 @pytest.mark.parametrize("inner", [F64, F32, F16])
 def test_multi_rhs_point_sources(method, inner):
+    """The 12 spin x colour columns of a point-source propagator, solved together
+    (on a 8^3 x 16 lattice; the 48^3 x 96 version is the propagator benchmark)."""
     # the spin x colour columns of a point-source propagator, solved together
     dims = (16, 8, 8, 8)
     kappa = 0.121
@@ -153,6 +156,16 @@ def test_multi_rhs_point_sources(method, inner):
         res = oracle_residual(U, b[r], x[r], kappa)
         assert res <= 1e-10, (r, res, infos[r].as_dict())
         assert abs(infos[r].true_rel_residual - res) < 1e-11
+
+
+@pytest.mark.parametrize("tile", [2, 4])
+def test_multi_rhs_cg_with_rhs_tiles(tile):
+    dims = (8, 4, 4, 8)
+    kappa = 0.12
+    srcs = [S.point_source(dims, s, c) for s in range(4) for c in range(3)]
+    U, b, x, infos = run_multi("cg", dims, 0.3, 9, kappa, F32, srcs, tile=tile)
+    for r in range(12):
+        assert oracle_residual(U, b[r], x[r], kappa) <= 1e-10
 
 
 def test_multi_rhs_matches_single_solves():
@@ -184,3 +197,69 @@ def test_multi_rhs_zero_and_nonzero_sources():
     assert np.all(x[1] == 0) and infos[1].iterations == 0
     for r in (0, 2):
         assert oracle_residual(U, b[r], x[r], kappa) <= 1e-10
+
+
+def test_batched_uneven_systems_one_launch():
+    """Several lattices, kappas and seeds solved by one persistent launch; each
+    solution checked with the oracle's operator."""
+    from paper_1405_0700_gb300 import plq as P
+
+    specs = S.batch_solve_specs(n=5, sizes=((8, 4, 4, 4), (16, 8, 8, 8), (10, 4, 6, 8)))
+    ctxs, xs, bs, Us, srcs = [], [], [], [], []
+    for sp in specs:
+        U, b = S.gauge_and_spinor(sp["dims"], sp["eps"], sp["seed"])
+        ctx = Context(sp["dims"])
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        ctxs.append(ctx)
+        bs.append(ctx.to_device(b, F64))
+        xs.append(ctx.empty_full(F64))
+        Us.append(U)
+        srcs.append(b)
+    infos, binfo = P.cg_solve_batched(ctxs, xs, bs, [sp["kappa"] for sp in specs], inner_prec=F32)
+    assert binfo["launches"] == 1
+    for k, sp in enumerate(specs):
+        x = ctxs[k].to_host(xs[k], F64)
+        res = oracle_residual(Us[k], srcs[k], x, sp["kappa"])
+        assert res <= 1e-10, (k, res, infos[k].as_dict())
+        assert abs(infos[k].true_rel_residual - res) < 1e-11
+    # uneven iteration counts: the systems really were independent
+    assert len({i.iterations for i in infos}) > 1
+    for c in ctxs:
+        c.close()
+
+
+@pytest.mark.parametrize("inner", [F64, F16])
+def test_batched_inner_precisions(inner):
+    from paper_1405_0700_gb300 import plq as P
+
+    dims = (8, 4, 4, 4)
+    U, b = S.gauge_and_spinor(dims, 0.3, 61)
+    ctx = Context(dims)
+    ctx.gauge_upload(U, 18, F64)
+    if inner == F16:
+        ctx.gauge_upload(U, 12, F16)
+    bd = ctx.to_device(b, F64)
+    x = ctx.empty_full(F64)
+    infos, binfo = P.cg_solve_batched([ctx], [x], [bd], [0.12], inner_prec=inner)
+    assert oracle_residual(U, b, ctx.to_host(x, F64), 0.12) <= 1e-10
+    ctx.close()
+
+
+def test_batched_zero_source_and_maxit():
+    from paper_1405_0700_gb300 import plq as P
+
+    dims = (8, 4, 4, 4)
+    U, b = S.gauge_and_spinor(dims, 0.3, 62)
+    ctx = Context(dims)
+    ctx.gauge_upload(U, 18, F64)
+    ctx.gauge_upload(U, 12, F32)
+    zero = ctx.to_device(np.zeros_like(b), F64)
+    x = ctx.empty_full(F64)
+    infos, _ = P.cg_solve_batched([ctx], [x], [zero], [0.12], inner_prec=F32)
+    assert not torch.any(x.view(torch.float64) != 0)
+    bd = ctx.to_device(b, F64)
+    with pytest.raises(PLQError) as e:
+        P.cg_solve_batched([ctx], [x], [bd], [0.12], inner_prec=F32, maxit=3)
+    assert e.value.status == plq.PLQ_ERR_NOT_CONVERGED
+    ctx.close()

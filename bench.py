@@ -229,6 +229,20 @@ def cg_section(torch, local_rank, quick):
             runs[name] = {"seconds": el, "iterations": info.iterations, "reliable_updates": info.n_reliable,
                           "true_rel_residual": info.true_rel_residual, "status": info.status}
             log(f"[bench] {name}: {el:.3f}s it={info.iterations} res={info.true_rel_residual:.2e}")
+        # reliable-update trigger: FP64 residual recomputations are expensive on
+        # this GPU, so the trade-off of delta is measured, not assumed
+        sweep = {}
+        for inner, pname in ((F32, "f32"), (F16, "f16")):
+            for delta in (0.1, 0.01, 0.001):
+                ctx.cg_solve(x, bd, kappa, tol=1e-10, inner_prec=inner, delta=delta, raise_on_error=False)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = ctx.cg_solve(x, bd, kappa, tol=1e-10, inner_prec=inner, delta=delta, raise_on_error=False)
+                torch.cuda.synchronize()
+                sweep[f"{pname}_delta{delta}"] = {"seconds": time.perf_counter() - t0, "iterations": info.iterations,
+                                                  "reliable_updates": info.n_reliable,
+                                                  "true_rel_residual": info.true_rel_residual}
+        out["delta_sweep"] = sweep
     out["runs"] = runs
     f64 = runs["cg_f64"]["seconds"]
     out["speedup_mixed_f32_vs_f64"] = f64 / runs["cg_mixed_f32"]["seconds"]
@@ -324,6 +338,50 @@ def propagator_section(torch, local_rank, quick):
     return out
 
 
+def operator_only(args, torch, local_rank):
+    from paper_1405_0700_gb300 import Context
+    from paper_1405_0700_gb300.plq import PREC_NAMES
+
+    dims = HOP_DIMS
+    if args.lattice:
+        lx, ly, lz, lt = (int(v) for v in args.lattice.lower().split("x"))
+        dims = (lt, lx, ly, lz)
+    prec, n = PREC_NAMES[args.prec], args.nrhs
+    U = S.gauge_field(dims, 0.2, 2)
+    vh = S.volume(dims) // 2
+    peak, _ = peaks()
+    with Context(dims, device=local_rank) as ctx:
+        ctx.gauge_upload(U, args.links, prec)
+        tuned = ctx.autotune(prec, n) if args.tune else None
+        if args.launch:
+            blk, mode, tile, zc = (int(v) for v in args.launch.split(","))
+            ctx.set_launch(prec, n, blk, mode, tile, zc)
+            tuned = {"block": blk, "index_mode": mode, "rhs_tile": tile, "z_chunk": zc}
+        inp = ctx.empty_half(prec, n)
+        inp.zero_()
+        out = ctx.empty_half(prec, n)
+        ms = time_hop(ctx, torch, prec, out, inp, args.steps, args.warmup) if n == 1 else None
+        if n > 1:
+            for _ in range(args.warmup):
+                ctx.hopping_eo(0, out, inp, prec, n)
+            torch.cuda.synchronize()
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record()
+            for _ in range(args.steps):
+                ctx.hopping_eo(0, out, inp, prec, n)
+            e_.record()
+            torch.cuda.synchronize()
+            ms = s_.elapsed_time(e_) / args.steps
+    link_b = {("f64", 18): 144, ("f64", 12): 96, ("f32", 18): 72, ("f32", 12): 48, ("f16", 18): 36,
+              ("f16", 12): 24}[(args.prec, args.links)]
+    sp = {"f64": 192, "f32": 96, "f16": 52}[args.prec]
+    per = 2 * sp + 8 * link_b / n
+    gbs = per * vh * n / (ms * 1e-3) / 1e9
+    print(json.dumps({"workload": "operator", "lattice": args.lattice or "32x32x32x64", "prec": args.prec,
+                      "links": args.links, "nrhs": n, "ms": ms, "gbs_compulsory": gbs, "frac": gbs / peak,
+                      "bytes_per_site_rhs": per, "launch": tuned}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,8 +391,13 @@ def main():
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small lattices (smoke use only)")
-    ap.add_argument("--workload", default="hop", choices=["hop", "propagator"],
+    ap.add_argument("--workload", default="hop", choices=["hop", "propagator", "operator"],
                     help="hop: the headline operator line (default); propagator: 48^3x96 with 12 point sources")
+    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"])
+    ap.add_argument("--links", type=int, default=18, choices=[18, 12])
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--tune", action="store_true", help="operator workload: autotune the launch first")
+    ap.add_argument("--launch", default=None, help="operator workload: block,index_mode,rhs_tile,z_chunk")
     ap.add_argument("--lattice", default=None,
                     help="LxxLyxLzxT for the operator workload (default 32x32x32x64); used for small profiling cases")
     args = ap.parse_args()
@@ -353,6 +416,9 @@ def main():
 
     torch.cuda.set_device(local_rank)
     lib()
+    if args.workload == "operator":
+        # one operator configuration alone (used for profiling): --lattice, --prec, --links, --nrhs
+        return operator_only(args, torch, local_rank)
     if args.workload == "propagator":
         res = propagator_section(torch, local_rank, args.quick)
         if rank == 0:

@@ -302,6 +302,7 @@ typedef struct {
     int block;            /* threads per block chosen                                      */
     int index_mode;       /* 0: neighbours from coordinates; 1: precomputed neighbour table */
     int rhs_tile;         /* right-hand sides per thread (each loaded link serves all)     */
+    int z_chunk;          /* site order: 0 = time slowest; z > 0 = z-chunks of z planes    */
     double us_per_launch; /* measured time of one half-lattice application                 */
     int from_cache;       /* 1 if the choice came from the cache file                      */
     int candidates;       /* configurations timed                                          */
@@ -314,7 +315,9 @@ typedef struct {
  * describes for out-of-order site access, Sec. 2.2), and for nrhs > 1 (FP32
  * and FP16 storage) with 2 or 4 right-hand sides per thread (register tiles
  * that reuse each loaded link, Sec. 2.3's one-matrix-two-vectors idea
- * widened), and keeps the fastest in
+ * widened) and with the sites walked in z-chunks of 8 or 4 planes (time
+ * inside a chunk, which keeps the data reused through the time direction
+ * within L2 for large multi-RHS fields), and keeps the fastest in
  * the context for every later operator and solver call of that precision.
  * cache_path (NULL: the PLQ_TUNE_CACHE environment variable, if set) names a
  * text file keyed by GPU name, lattice, precision, link format and nrhs: a
@@ -324,9 +327,39 @@ typedef struct {
 PLQ_API plq_status plq_autotune(plq_ctx *ctx, int prec, int nrhs, const char *cache_path, plq_tune_result *res);
 
 /* Set the hopping launch of (prec, nrhs) by hand: block = threads per block
- * (0 = library default, else a multiple of 32 up to 256), index_mode 0 or 1
- * and rhs_tile 1, 2 or 4 (dividing nrhs) as above. */
-PLQ_API plq_status plq_set_launch(plq_ctx *ctx, int prec, int nrhs, int block, int index_mode, int rhs_tile);
+ * (0 = library default, else a multiple of 32 up to 256), index_mode 0 or 1,
+ * rhs_tile 1, 2 or 4 (dividing nrhs) and z_chunk 0 or a divisor of Lz, as
+ * above. */
+PLQ_API plq_status plq_set_launch(plq_ctx *ctx, int prec, int nrhs, int block, int index_mode, int rhs_tile,
+                                  int z_chunk);
+
+/* Two-pass schedule of the hopping operator through the auxiliary fields of
+ * Eq. (2): pass 1 computes, at every input site y, theta+_mu(y) = (1 -
+ * gamma_mu) phi(y) and theta-_mu(y) = U_mu(y)^dagger (1 + gamma_mu) phi(y)
+ * (upper two spin components only, the remark after Eq. (2)); pass 2
+ * gathers psi(x) = sum_mu [U_mu(x) theta+_mu(x + mu) + theta-_mu(x - mu)].
+ * This is the order of operations the paper's distributed code uses to
+ * overlap the boundary exchange of theta with bulk work (Sec. 2.2); on one
+ * GPU it is a comparison point for the fused plq_hopping_eo (same result,
+ * twice the memory traffic).  `theta` is a caller-owned device buffer of
+ * plq_theta_bytes(ctx, prec) bytes.  FP64 and FP32 only; nrhs = 1. */
+PLQ_API size_t plq_theta_bytes(const plq_ctx *ctx, int prec);
+PLQ_API plq_status plq_hopping_eo_theta(plq_ctx *ctx, int out_parity, void *out, const void *in, void *theta,
+                                        int prec, void *stream);
+
+/* Link x spinor streaming micro-benchmark (the paper's prefetch / access
+ * pattern experiment, Sec. 2.2): psi(i) = U(i) phi(i) -- one SU(3) matrix on
+ * the four colour vectors of a spinor -- for nsites records stored site by
+ * site (18 reals of U, 24 of phi and psi; prec PLQ_F64 or PLQ_F32).
+ *   mode 0: sequential, record i;
+ *   mode 1: random through the device index array `index` (record index[i];
+ *           entries outside [0, nsites) are skipped);
+ *   mode 2: random through precomputed device pointer arrays `pointers`
+ *           (3*nsites entries: psi'(i), then U'(i), then phi'(i)), which the
+ *           caller must fill with addresses of valid records.
+ * Asynchronous on `stream`; the caller times it. */
+PLQ_API plq_status plq_link_spinor_stream(int mode, long long nsites, const void *U, const void *phi, void *psi,
+                                          const int *index, const void *const *pointers, int prec, void *stream);
 
 /* Roofline calibration (a measurement helper; the paper has no counterpart):
  * the sustained FMA throughput of the CUDA cores of `device` in FP64

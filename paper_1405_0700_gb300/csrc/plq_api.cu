@@ -338,6 +338,7 @@ plq_status plq_hopping_eo_host(plq_ctx *c, int out_parity, void *out_host, const
         HopArgs a = hop_args(c, prec, out_parity, dout, din, nrhs);
         a.site_begin = chunk_t0(k) * slab;
         a.site_end = chunk_t0(k + 1) * slab;
+        a.zc = 0;  // site ranges are in checkerboard order
         PLQ_TRY(launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, c->compute));
         PLQ_CUDA(cudaEventRecord(ev_done[k], c->compute));
         PLQ_CUDA(cudaStreamWaitEvent(c->copy_out, ev_done[k], 0));

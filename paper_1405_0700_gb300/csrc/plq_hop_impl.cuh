@@ -217,7 +217,20 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
 
     const int r0 = threadIdx.x * RT;
     const int i_end = a.site_end < 0 ? a.lat.Vh : a.site_end;
-    for (int i = a.site_begin + blockIdx.x * blockDim.y + threadIdx.y; i < i_end; i += gridDim.x * blockDim.y) {
+    const int plane = a.lat.L[2] * (a.lat.L[1] >> 1);  // checkerboard sites of one (t, z) plane
+    const int zc = a.zc;
+    for (int li = a.site_begin + blockIdx.x * blockDim.y + threadIdx.y; li < i_end; li += gridDim.x * blockDim.y) {
+        int i = li;
+        if (zc > 0) {  // z-chunk order: (chunk, t, z in chunk, y, x)
+            const int per_chunk = a.lat.L[0] * zc * plane;
+            const int c = li / per_chunk;
+            int rem = li - c * per_chunk;
+            const int t = rem / (zc * plane);
+            rem -= t * zc * plane;
+            const int zi = rem / plane;
+            const int w = rem - zi * plane;
+            i = (t * a.lat.L[3] + c * zc + zi) * plane + w;
+        }
         bool all_frozen = a.st != nullptr;
 #pragma unroll
         for (int t = 0; t < RT; ++t) all_frozen = all_frozen && a.st[r0 + t].stop;

@@ -102,6 +102,7 @@ struct TuneEntry {
     int block = 0;       // 0 = default
     int index_mode = 0;  // 0 inline coordinates, 1 neighbour table
     int rhs_tile = 1;    // right-hand sides per thread
+    int zc = 0;          // z-chunk site order (0 = natural)
     float us = 0.f;
 };
 
@@ -164,6 +165,11 @@ struct HopArgs {
     const int *nbr = nullptr;
     int block = 0;  // threads per block; 0 = default
     int rhs_tile = 1;  // right-hand sides per thread (1, 2 or 4; must divide nrhs)
+    // Site order: 0 = checkerboard order (t slowest).  zc > 0 walks the lattice
+    // in z-chunks of zc planes (t runs inside a chunk), which shrinks the span
+    // of input data reused through the time direction to zc/Lz of a time
+    // slab per slice -- what keeps multi-RHS neighbour reuse inside L2.
+    int zc = 0;
     // Twisted-mass epilogue terms (0 = plain Wilson): the hopping result is
     // replaced by scale_h * (1 + i nu_h gamma5) H in, and the xpay source x by
     // (1 + i nu_x gamma5) x.

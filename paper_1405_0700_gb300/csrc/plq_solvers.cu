@@ -375,16 +375,30 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
                 init[r].stop = done[r];
             }
             if (method == SOLVER_CG) {
-                // r = Mhat^dag s, the residual of the normal equations
-                if ((st = hop(S, PLQ_F64, 1, tmp_o64, s64, EPI_PLAIN, 1, nullptr, 0.0, FIN_NONE, nullptr, false,
-                              tw_first(S, true))) != PLQ_OK)
-                    break;
-                if ((st = hop(S, PLQ_F64, 0, r64, tmp_o64, EPI_XPAY_NORM, 1, s64, -kappa * kappa, FIN_NONE, nullptr,
-                              false, tw_second(S, true))) != PLQ_OK)
-                    break;
-                if ((st = read_sums(S, r2.data(), n)) != PLQ_OK) break;
+                // r = Mhat^dag s, the residual of the normal equations.  s is the
+                // FP64 true residual; r only restarts the inner iteration, so with
+                // a low-precision inner solve it is formed at that precision (two
+                // inner-precision half-applies instead of two FP64 ones).
                 void *rL = L[0], *pL = L[1], *qL = L[2], *mpL = L[3], *toL = L[4];
-                if ((st = blas_copy_convert(S.N, rL, S.P, r64, PLQ_F64, s)) != PLQ_OK) break;
+                if (S.P == PLQ_F64) {
+                    if ((st = hop(S, PLQ_F64, 1, tmp_o64, s64, EPI_PLAIN, 1, nullptr, 0.0, FIN_NONE, nullptr, false,
+                                  tw_first(S, true))) != PLQ_OK)
+                        break;
+                    if ((st = hop(S, PLQ_F64, 0, r64, tmp_o64, EPI_XPAY_NORM, 1, s64, -kappa * kappa, FIN_NONE,
+                                  nullptr, false, tw_second(S, true))) != PLQ_OK)
+                        break;
+                    if ((st = blas_copy_convert(S.N, rL, S.P, r64, PLQ_F64, s)) != PLQ_OK) break;
+                } else {
+                    void *sL = mpL;  // free until the inner iteration starts
+                    if ((st = blas_copy_convert(S.N, sL, S.P, s64, PLQ_F64, s)) != PLQ_OK) break;
+                    if ((st = hop(S, S.P, 1, toL, sL, EPI_PLAIN, 1, nullptr, 0.0, FIN_NONE, nullptr, false,
+                                  tw_first(S, true))) != PLQ_OK)
+                        break;
+                    if ((st = hop(S, S.P, 0, rL, toL, EPI_XPAY_NORM, 1, sL, -kappa * kappa, FIN_NONE, nullptr, false,
+                                  tw_second(S, true))) != PLQ_OK)
+                        break;
+                }
+                if ((st = read_sums(S, r2.data(), n)) != PLQ_OK) break;
                 if ((st = blas_zero(S.N, xL, S.PX, s)) != PLQ_OK) break;
                 for (int r = 0; r < n; ++r) {
                     if (done[r]) continue;

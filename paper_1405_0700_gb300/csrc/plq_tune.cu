@@ -49,12 +49,13 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         char k[600];
-        int block = 0, mode = 0, tile = 1;
+        int block = 0, mode = 0, tile = 1, zc = 0;
         float us = 0;
-        if (sscanf(line, "%599s %d %d %d %f", k, &block, &mode, &tile, &us) == 5 && key == k) {
+        if (sscanf(line, "%599s %d %d %d %d %f", k, &block, &mode, &tile, &zc, &us) == 6 && key == k) {
             e->block = block;
             e->index_mode = mode;
             e->rhs_tile = tile;
+            e->zc = zc;
             e->us = us;
             found = true;  // last entry wins
         }
@@ -66,7 +67,7 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
 void cache_store(const char *path, const std::string &key, const TuneEntry &e) {
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %.3f\n", key.c_str(), e.block, e.index_mode, e.rhs_tile, e.us);
+    fprintf(f, "%s %d %d %d %d %.3f\n", key.c_str(), e.block, e.index_mode, e.rhs_tile, e.zc, e.us);
     fclose(f);
 }
 
@@ -90,6 +91,7 @@ void apply_tune(const Ctx *c, int prec, int nrhs, HopArgs &a) {
     if (e.block > 0) a.block = e.block;
     a.nbr = (e.index_mode == 1) ? c->nbr[a.out_parity] : nullptr;
     a.rhs_tile = (e.rhs_tile > 1 && nrhs % e.rhs_tile == 0) ? e.rhs_tile : 1;
+    a.zc = (e.zc > 0 && c->lat.L[3] % e.zc == 0) ? e.zc : 0;
 }
 
 }  // namespace plq
@@ -113,6 +115,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
             res->block = best.block;
             res->index_mode = best.index_mode;
             res->rhs_tile = best.rhs_tile;
+            res->z_chunk = best.zc;
             res->us_per_launch = best.us;
             res->from_cache = 1;
         }
@@ -140,14 +143,21 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
     const int reps = 10;
     // candidates: index mode x block size, plus right-hand-side tiles for nrhs > 1
     struct Cand {
-        int mode, tile;
+        int mode, tile, zc;
     };
-    Cand cands[8];
+    Cand cands[24];
     int nc = 0;
-    cands[nc++] = {0, 1};
-    cands[nc++] = {1, 1};
-    if (prec != PLQ_F64 && nrhs % 2 == 0) cands[nc++] = {0, 2};
-    if (prec != PLQ_F64 && nrhs % 4 == 0) cands[nc++] = {0, 4};
+    const int Lz = c->lat.L[3];
+    int zcs[3] = {0, 0, 0}, nz = 1;
+    for (int z : {8, 4})
+        if (z < Lz && Lz % z == 0) zcs[nz++] = z;
+    for (int zi = 0; zi < nz; ++zi) {
+        const int z = zcs[zi];
+        cands[nc++] = {0, 1, z};
+        if (z == 0) cands[nc++] = {1, 1, 0};
+        if (prec != PLQ_F64 && nrhs % 2 == 0) cands[nc++] = {0, 2, z};
+        if (prec != PLQ_F64 && nrhs % 4 == 0) cands[nc++] = {0, 4, z};
+    }
     for (int ci = 0; ci < nc && st == PLQ_OK; ++ci) {
         const int mode = cands[ci].mode;
         for (int b : blocks) {
@@ -162,6 +172,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
             a.block = b;
             a.nbr = mode ? c->nbr[0] : nullptr;
             a.rhs_tile = cands[ci].tile;
+            a.zc = cands[ci].zc;
             for (int w = 0; w < 2 && st == PLQ_OK; ++w) st = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
             cudaEventRecord(e0, s);
             for (int r = 0; r < reps && st == PLQ_OK; ++r) st = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
@@ -181,6 +192,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
                 best.block = b;
                 best.index_mode = mode;
                 best.rhs_tile = cands[ci].tile;
+                best.zc = cands[ci].zc;
             }
         }
     }
@@ -196,6 +208,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
         res->block = best.block;
         res->index_mode = best.index_mode;
         res->rhs_tile = best.rhs_tile;
+        res->z_chunk = best.zc;
         res->us_per_launch = best.us;
         res->from_cache = 0;
         res->candidates = tried;
@@ -203,7 +216,8 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
     return PLQ_OK;
 }
 
-extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, int index_mode, int rhs_tile) {
+extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, int index_mode, int rhs_tile,
+                                     int z_chunk) {
     if (!c) return set_error(PLQ_ERR_ARG, "null context");
     if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
     if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
@@ -212,10 +226,13 @@ extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, 
     if (index_mode != 0 && index_mode != 1) return set_error(PLQ_ERR_ARG, "index_mode must be 0 or 1");
     if (rhs_tile != 1 && rhs_tile != 2 && rhs_tile != 4) return set_error(PLQ_ERR_ARG, "rhs_tile must be 1, 2 or 4");
     if (nrhs % rhs_tile) return set_error(PLQ_ERR_ARG, "rhs_tile must divide nrhs");
+    if (z_chunk < 0 || (z_chunk > 0 && c->lat.L[3] % z_chunk))
+        return set_error(PLQ_ERR_ARG, "z_chunk must be 0 or divide Lz");
     PLQ_CUDA(cudaSetDevice(c->device));
     if (index_mode == 1) PLQ_TRY(ensure_nbr_tables(c));
     c->tune[prec][nrhs].block = block;
     c->tune[prec][nrhs].index_mode = index_mode;
     c->tune[prec][nrhs].rhs_tile = rhs_tile;
+    c->tune[prec][nrhs].zc = z_chunk;
     return PLQ_OK;
 }

@@ -53,6 +53,7 @@ class TuneResult(ctypes.Structure):
         ("block", ctypes.c_int),
         ("index_mode", ctypes.c_int),
         ("rhs_tile", ctypes.c_int),
+        ("z_chunk", ctypes.c_int),
         ("us_per_launch", ctypes.c_double),
         ("from_cache", ctypes.c_int),
         ("candidates", ctypes.c_int),
@@ -114,10 +115,13 @@ SIGNATURES = {
     "plq_cg_solve_batched": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolverParams),
                                       ctypes.POINTER(SolveInfo), ctypes.POINTER(BatchInfo), _vp]),
+    "plq_theta_bytes": (_c_size, [_vp, _c_int]),
+    "plq_hopping_eo_theta": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _c_int, _vp]),
+    "plq_link_spinor_stream": (_c_int, [_c_int, ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _c_int, _vp]),
     "plq_measure_fma_rate": (_c_int, [_c_int, _c_int, ctypes.POINTER(ctypes.c_double)]),
     "plq_schur_apply_noalloc": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, _c_int, _vp]),
     "plq_autotune": (_c_int, [_vp, _c_int, _c_int, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
-    "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int]),
+    "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int]),
 }
 
 _lib = None
@@ -307,6 +311,15 @@ class Context:
                                             prec_of(prec), _stream(stream)))
         return out
 
+    def theta_bytes(self, prec):
+        return int(lib().plq_theta_bytes(self._h, prec_of(prec)))
+
+    def hopping_eo_theta(self, out_parity, out, inp, theta, prec, stream=None):
+        """Two-pass (theta-field) schedule of the half-lattice hopping operator."""
+        check(lib().plq_hopping_eo_theta(self._h, out_parity, _ptr(out), _ptr(inp), _ptr(theta), prec_of(prec),
+                                         _stream(stream)))
+        return out
+
     # ------------------------------------------------------------ tuning
     def autotune(self, prec, nrhs=1, cache_path=None):
         r = TuneResult()
@@ -314,8 +327,8 @@ class Context:
         check(lib().plq_autotune(self._h, prec_of(prec), nrhs, path, ctypes.byref(r)))
         return r.as_dict()
 
-    def set_launch(self, prec, nrhs=1, block=0, index_mode=0, rhs_tile=1):
-        check(lib().plq_set_launch(self._h, prec_of(prec), nrhs, block, index_mode, rhs_tile))
+    def set_launch(self, prec, nrhs=1, block=0, index_mode=0, rhs_tile=1, z_chunk=0):
+        check(lib().plq_set_launch(self._h, prec_of(prec), nrhs, block, index_mode, rhs_tile, z_chunk))
 
     # ------------------------------------------------------------ solvers
     def _solve(self, fn, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every, stream, raise_on_error,
@@ -375,6 +388,12 @@ def cg_solve_batched(ctxs, xs, bs, kappas, tol=1e-10, maxit=20000, inner_prec=F6
     if raise_on_error:
         check(st, (list(infos), bi))
     return list(infos), bi.as_dict()
+
+
+def link_spinor_stream(mode, nsites, U, phi, psi, index=None, pointers=None, prec=F32, stream=None):
+    """psi(i) = U(i) phi(i) over nsites site records (see plq_link_spinor_stream)."""
+    check(lib().plq_link_spinor_stream(int(mode), int(nsites), _ptr(U), _ptr(phi), _ptr(psi), _ptr(index),
+                                       _ptr(pointers), prec_of(prec), _stream(stream)))
 
 
 def measure_fma_rate(prec, device=0):

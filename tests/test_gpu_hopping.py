@@ -116,18 +116,18 @@ def test_multi_rhs(nrhs, prec, reals):
         assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
 
 
-@pytest.mark.parametrize("tile", [2, 4])
+@pytest.mark.parametrize("tile,zc", [(2, 0), (4, 0), (1, 2), (2, 4)])
 @pytest.mark.parametrize("prec,reals", [(F32, 18), (F32, 12), (F16, 12), (F16, 18)])
-def test_multi_rhs_tiles(tile, prec, reals):
-    # each thread applies every link it loads to `tile` right-hand sides
-    dims = (6, 4, 2, 4)
+def test_multi_rhs_tiles(tile, zc, prec, reals):
+    # each thread applies every link it loads to `tile` right-hand sides; zc walks the
+    # sites in z-chunks
+    dims = (6, 4, 2, 8)
     nrhs = 12
     U = S.gauge_field(dims, 0.3, 16)
     phis = np.stack([S.gaussian_spinor(dims, 200 + r) for r in range(nrhs)])
-    kappa = 0.11
     with Context(dims) as ctx:
         ctx.gauge_upload(U, reals, prec)
-        ctx.set_launch(prec, nrhs, 96, 0, tile)
+        ctx.set_launch(prec, nrhs, 96, 0, tile, zc)
         got = gpu_hopping_full(ctx, phis, prec, nrhs).reshape(phis.shape)
     for r in range(nrhs):
         assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
@@ -204,7 +204,7 @@ def test_neighbour_table_mode_matches_oracle(prec):
     kappa = 0.12
     with Context(dims) as ctx:
         ctx.gauge_upload(U, 12 if prec == F16 else 18, prec)
-        ctx.set_launch(prec, 1, 64, 1)
+        ctx.set_launch(prec, 1, 64, 1, 1, 2)
         got = gpu_hopping_full(ctx, phi, prec)
         inp = ctx.to_device(phi, prec)
         out = ctx.empty_full(prec)
@@ -221,7 +221,7 @@ def test_autotune_and_cache(tmp_path):
     with Context(dims) as ctx:
         ctx.gauge_upload(U, 18, F32)
         r = ctx.autotune(F32, 1, cache_path=cache)
-        assert r["from_cache"] == 0 and r["candidates"] == 10 and r["block"] in (64, 96, 128, 192, 256)
+        assert r["from_cache"] == 0 and r["candidates"] >= 10 and r["block"] in (64, 96, 128, 192, 256)
         got = gpu_hopping_full(ctx, phi, F32)  # runs with the tuned launch
         assert rel(got, W.hopping(U, phi)) <= TOL[F32]
     with Context(dims) as ctx:

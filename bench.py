@@ -179,6 +179,20 @@ def run_reference(args, rank):
 METRIC = "hopping-op GFLOP/s (1320 flop/site, 32^3x64 half-apply, FP32 storage, 18-real links)"
 
 
+def aggregate_over_ranks(ms_local, units_local, dist=None, device="cpu"):
+    """Whole-job figures of a replica run: the slowest rank's time (max over
+    ranks) and the units of work summed over ranks."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(ms_local), float(units_local)
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ------------------------------------------------------------------ GPU arm
 def time_hop(ctx, torch, prec, out, inp, steps, warmup, parity=0):
     for _ in range(warmup):
@@ -354,9 +368,10 @@ def operator_only(args, torch, local_rank):
         ctx.gauge_upload(U, args.links, prec)
         tuned = ctx.autotune(prec, n) if args.tune else None
         if args.launch:
-            blk, mode, tile, zc = (int(v) for v in args.launch.split(","))
-            ctx.set_launch(prec, n, blk, mode, tile, zc)
-            tuned = {"block": blk, "index_mode": mode, "rhs_tile": tile, "z_chunk": zc}
+            vals = [int(v) for v in args.launch.split(",")] + [0]
+            blk, mode, tile, zc, sm = vals[:5]
+            ctx.set_launch(prec, n, blk, mode, tile, zc, sm)
+            tuned = {"block": blk, "index_mode": mode, "rhs_tile": tile, "z_chunk": zc, "smem_links": sm}
         inp = ctx.empty_half(prec, n)
         inp.zero_()
         out = ctx.empty_half(prec, n)
@@ -382,6 +397,104 @@ def operator_only(args, torch, local_rank):
                       "bytes_per_site_rhs": per, "launch": tuned}), flush=True)
 
 
+def eigcg_section(torch, local_rank, quick):
+    """The paper's Sec. 3 protocol on a synthetic field: incremental EigCG with
+    nev = 10, m = 60 over the first 30 right-hand sides (300 vectors), FP64,
+    tolerance 1e-8, then deflated CG; plain CG on the same sources for comparison."""
+    from paper_1405_0700_gb300 import F64, Context
+    from paper_1405_0700_gb300.plq import EigCG
+
+    dims = (48, 24, 24, 24) if not quick else (16, 8, 8, 8)
+    # a smooth field near the critical kappa: isolated low modes, as for the
+    # light-quark systems the paper deflates (its ETMC configuration is not available)
+    kappa, eps, seed = 0.1255, 0.05, 6
+    n_rhs, n_acc, nev, m = (35, 30, 10, 60) if not quick else (8, 5, 4, 20)
+    U = S.gauge_field(dims, eps, seed)
+    out = {"lattice": "x".join(map(str, dims[1:])) + "x" + str(dims[0]), "kappa": kappa, "eps": eps, "seed": seed,
+           "nev": nev, "m": m, "rhs": n_rhs, "accumulated": n_acc, "tol": 1e-8, "precision": "f64"}
+    rows = []
+    with Context(dims, device=local_rank) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        eig = EigCG(ctx, nev=nev, m=m, max_vectors=nev * n_acc)
+        for k in range(n_rhs):
+            b = ctx.to_device(S.gaussian_spinor(dims, 7000 + k), F64)
+            x = ctx.empty_full(F64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = eig.solve(x, b, kappa, tol=1e-8, accumulate=k < n_acc, raise_on_error=False)
+            torch.cuda.synchronize()
+            te = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            # plain CG on the same source (no deflation): FP64 normal-equation CG via a fresh handle
+            plain = EigCG(ctx, nev=nev, m=m, max_vectors=nev)
+            info_p = plain.solve(x, b, kappa, tol=1e-8, accumulate=False, raise_on_error=False)
+            torch.cuda.synchronize()
+            tp = time.perf_counter() - t0
+            plain.close()
+            rows.append({"rhs": k, "eigcg_seconds": te, "eigcg_iterations": info.iterations,
+                         "vectors": info.n_reliable, "cg_seconds": tp, "cg_iterations": info_p.iterations,
+                         "eigcg_residual": info.true_rel_residual, "cg_residual": info_p.true_rel_residual})
+            log(f"[bench] eigcg rhs {k}: {te:.2f}s it={info.iterations} vec={info.n_reliable} | cg {tp:.2f}s "
+                f"it={info_p.iterations}")
+        eig.close()
+    out["per_rhs"] = rows
+    tail = rows[n_acc:]
+    if tail:
+        out["speedup_after_accumulation"] = float(np.mean([r["cg_seconds"] for r in tail]) /
+                                                  np.mean([r["eigcg_seconds"] for r in tail]))
+        out["iteration_ratio_after_accumulation"] = float(np.mean([r["cg_iterations"] for r in tail]) /
+                                                          np.mean([r["eigcg_iterations"] for r in tail]))
+    return out
+
+
+def batch_section(torch, local_rank, quick):
+    """16 independent solves of uneven lattices (8^3x16, 16^3x32, 24^3x48), kappa in
+    [0.110, 0.124], in ONE persistent graph-captured launch vs the same 16 solves one
+    after the other; mixed FP32-inner CG to a true residual of 1e-10."""
+    from paper_1405_0700_gb300 import F32, F64, Context
+    from paper_1405_0700_gb300 import plq as P
+
+    specs = S.batch_solve_specs(n=16 if not quick else 4)
+    ctxs, xs, bs = [], [], []
+    for sp in specs:
+        U, b = S.gauge_and_spinor(sp["dims"], sp["eps"], sp["seed"])
+        ctx = Context(sp["dims"], device=local_rank)
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        ctxs.append(ctx)
+        bs.append(ctx.to_device(b, F64))
+        xs.append(ctx.empty_full(F64))
+    kappas = [sp["kappa"] for sp in specs]
+    P.cg_solve_batched(ctxs, xs, bs, kappas, inner_prec=F32, raise_on_error=False)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos, binfo = P.cg_solve_batched(ctxs, xs, bs, kappas, inner_prec=F32, raise_on_error=False)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    for ctx in ctxs:
+        ctx.autotune(F32, 1)
+    seq = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ctx, x, b, k in zip(ctxs, xs, bs, kappas):
+        seq.append(ctx.cg_solve(x, b, k, inner_prec=F32, raise_on_error=False))
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    out = {"solves": len(specs), "lattices": [("x".join(map(str, sp["dims"][1:])) + "x" + str(sp["dims"][0]))
+                                              for sp in specs],
+           "kappas": kappas, "persistent": {"seconds": t_batch, **binfo,
+                                            "iterations": [i.iterations for i in infos],
+                                            "true_rel_residual": [i.true_rel_residual for i in infos],
+                                            "status": [i.status for i in infos]},
+           "sequential": {"seconds": t_seq, "iterations": [i.iterations for i in seq],
+                          "true_rel_residual": [i.true_rel_residual for i in seq]},
+           "speedup_persistent_vs_sequential": t_seq / t_batch}
+    for c in ctxs:
+        c.close()
+    log(f"[bench] batch of {len(specs)}: persistent {t_batch:.3f}s ({binfo}) vs sequential {t_seq:.3f}s")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,13 +504,13 @@ def main():
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small lattices (smoke use only)")
-    ap.add_argument("--workload", default="hop", choices=["hop", "propagator", "operator"],
+    ap.add_argument("--workload", default="hop", choices=["hop", "propagator", "operator", "eigcg", "batch"],
                     help="hop: the headline operator line (default); propagator: 48^3x96 with 12 point sources")
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"])
     ap.add_argument("--links", type=int, default=18, choices=[18, 12])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--tune", action="store_true", help="operator workload: autotune the launch first")
-    ap.add_argument("--launch", default=None, help="operator workload: block,index_mode,rhs_tile,z_chunk")
+    ap.add_argument("--launch", default=None, help="operator workload: block,index_mode,rhs_tile,z_chunk[,smem]")
     ap.add_argument("--lattice", default=None,
                     help="LxxLyxLzxT for the operator workload (default 32x32x32x64); used for small profiling cases")
     args = ap.parse_args()
@@ -419,6 +532,16 @@ def main():
     if args.workload == "operator":
         # one operator configuration alone (used for profiling): --lattice, --prec, --links, --nrhs
         return operator_only(args, torch, local_rank)
+    if args.workload == "batch":
+        res = batch_section(torch, local_rank, args.quick)
+        if rank == 0:
+            print(json.dumps({"workload": "batch", **res}), flush=True)
+        return
+    if args.workload == "eigcg":
+        res = eigcg_section(torch, local_rank, args.quick)
+        if rank == 0:
+            print(json.dumps({"workload": "eigcg", **res}), flush=True)
+        return
     if args.workload == "propagator":
         res = propagator_section(torch, local_rank, args.quick)
         if rank == 0:
@@ -462,14 +585,9 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms_total = start.elapsed_time(end)
-    if dist:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total, sites_all = aggregate_over_ranks(start.elapsed_time(end), vh * args.steps, dist, "cuda")
     ms = ms_total / args.steps
-    gflops_rank = FLOP_PER_SITE * vh / (ms * 1e-3) / 1e9
-    value = gflops_rank * world
+    value = FLOP_PER_SITE * sites_all / (ms_total * 1e-3) / 1e9
     head = roofline_entry(ms, vh, "f32", 18, peak)
 
     # ---- e2e: host buffers through plq_hopping_eo_host

@@ -109,7 +109,8 @@ typedef struct {
     int inner_prec;    /* PLQ_F64 (plain FP64 solve), PLQ_F32 or PLQ_F16 inner precision   */
     double delta;      /* reliable-update trigger: the FP64 residual is recomputed when the
                           inner residual fell by this factor since the last update;
-                          default 0.1 (ignored when inner_prec == PLQ_F64)                  */
+                          default 1e-3 for FP32, 1e-2 for FP16 inner solves (ignored when
+                          inner_prec == PLQ_F64)                                            */
     int use_x0;        /* 1: x holds an initial guess on entry (resume); 0: start from 0   */
     int check_every;   /* inner iterations per host convergence poll, default 16           */
     double mu;         /* twisted mass: solve M_tm = 1 - kappa H + 2 i kappa mu gamma5
@@ -241,6 +242,31 @@ PLQ_API plq_status plq_cg_solve_multi(plq_ctx *ctx, void *x, const void *b, doub
 PLQ_API plq_status plq_bicgstab_solve_multi(plq_ctx *ctx, void *x, const void *b, double kappa, int nrhs,
                                             const plq_solver_params *params, plq_solve_info *infos, void *stream);
 
+/* Incremental EigCG: the deflation solver of the paper's Sec. 3 (Stathopoulos
+ * and Orginos' eigCG; the paper's runs use nev = 10, m = 60, 30 right-hand
+ * sides for 300 vectors, FP64, relative tolerance 1e-8).  A handle holds a
+ * growing orthonormal basis U of approximate low eigenvectors of A =
+ * Mhat^dag Mhat (even-odd normal equations) and H = U^H A U.
+ *   plq_eigcg_create: nev Ritz vectors per accumulating solve, search space m
+ *     (2*nev + 2 <= m <= 64, 2*nev <= 24), room for max_vectors basis vectors
+ *     (device memory: max_vectors + 2*(m+1) + 4 FP64 half fields).
+ *   plq_eigcg_solve: solves M x = b (packed full FP64 fields).  The Krylov
+ *     solve on the normal equations starts from the Galerkin guess
+ *     x0 = U H^{-1} U^H rhs; with accumulate != 0 (and room left in U) it is
+ *     eigCG and its nev lowest Ritz vectors are added to U afterwards,
+ *     otherwise plain CG.  Stops when the normal-equation residual falls to
+ *     params->tol (default 1e-8) relative to its right-hand side; info reports
+ *     the true residual ||b - M x|| / ||b|| and, in n_reliable, the number of
+ *     basis vectors now held.  FP64 throughout; Wilson operator (mu = 0).
+ *   plq_eigcg_vectors: basis vectors held. */
+typedef struct plq_eigcg plq_eigcg;
+PLQ_API plq_status plq_eigcg_create(plq_ctx *ctx, int nev, int m, int max_vectors, plq_eigcg **out);
+PLQ_API plq_status plq_eigcg_destroy(plq_eigcg *eig);
+PLQ_API int plq_eigcg_vectors(const plq_eigcg *eig);
+PLQ_API plq_status plq_eigcg_solve(plq_eigcg *eig, void *x, const void *b, double kappa,
+                                   const plq_solver_params *params, int accumulate, plq_solve_info *info,
+                                   void *stream);
+
 /* Launch report of plq_cg_solve_batched. */
 typedef struct {
     int grid;            /* blocks of the persistent kernel (all co-resident)  */
@@ -303,6 +329,7 @@ typedef struct {
     int index_mode;       /* 0: neighbours from coordinates; 1: precomputed neighbour table */
     int rhs_tile;         /* right-hand sides per thread (each loaded link serves all)     */
     int z_chunk;          /* site order: 0 = time slowest; z > 0 = z-chunks of z planes    */
+    int smem_links;       /* nrhs > 1: links of a block of sites staged in shared memory  */
     double us_per_launch; /* measured time of one half-lattice application                 */
     int from_cache;       /* 1 if the choice came from the cache file                      */
     int candidates;       /* configurations timed                                          */
@@ -315,7 +342,8 @@ typedef struct {
  * describes for out-of-order site access, Sec. 2.2), and for nrhs > 1 (FP32
  * and FP16 storage) with 2 or 4 right-hand sides per thread (register tiles
  * that reuse each loaded link, Sec. 2.3's one-matrix-two-vectors idea
- * widened) and with the sites walked in z-chunks of 8 or 4 planes (time
+ * widened), with the links of a block of sites staged once in shared memory
+ * (nrhs > 1), and with the sites walked in z-chunks of 8 or 4 planes (time
  * inside a chunk, which keeps the data reused through the time direction
  * within L2 for large multi-RHS fields), and keeps the fastest in
  * the context for every later operator and solver call of that precision.
@@ -328,10 +356,10 @@ PLQ_API plq_status plq_autotune(plq_ctx *ctx, int prec, int nrhs, const char *ca
 
 /* Set the hopping launch of (prec, nrhs) by hand: block = threads per block
  * (0 = library default, else a multiple of 32 up to 256), index_mode 0 or 1,
- * rhs_tile 1, 2 or 4 (dividing nrhs) and z_chunk 0 or a divisor of Lz, as
- * above. */
+ * rhs_tile 1, 2 or 4 (dividing nrhs), z_chunk 0 or a divisor of Lz and
+ * smem_links 0/1 (nrhs > 1, FP32/FP16; with it rhs_tile 1 or 2), as above. */
 PLQ_API plq_status plq_set_launch(plq_ctx *ctx, int prec, int nrhs, int block, int index_mode, int rhs_tile,
-                                  int z_chunk);
+                                  int z_chunk, int smem_links);
 
 /* Two-pass schedule of the hopping operator through the auxiliary fields of
  * Eq. (2): pass 1 computes, at every input site y, theta+_mu(y) = (1 -

@@ -507,9 +507,6 @@ plq_status launch_batched(const BatchArgs &args, cudaStream_t s, int *grid_out, 
 
 }  // namespace
 
-plq_status wilson_residual64(plq_ctx *c, double kappa, const void *x, const void *b, double *r2, double *b2,
-                             cudaStream_t s);
-
 }  // namespace plq
 
 using namespace plq;
@@ -524,7 +521,9 @@ extern "C" plq_status plq_cg_solve_batched(plq_ctx **ctxs, int n, void **x, cons
     const double tol = (params && params->tol > 0) ? params->tol : 1e-10;
     const int maxit = (params && params->maxit > 0) ? params->maxit : 20000;
     const int inner = params ? params->inner_prec : PLQ_F64;
-    const double delta = inner == PLQ_F64 ? 0.0 : ((params && params->delta > 0) ? params->delta : 0.1);
+    const double delta = inner == PLQ_F64 ? 0.0
+                                           : ((params && params->delta > 0) ? params->delta
+                                                                            : (inner == PLQ_F16 ? 1e-2 : 1e-3));
     const int use_x0 = params ? params->use_x0 : 0;
     if (!valid_prec(inner)) return set_error(PLQ_ERR_ARG, "bad inner precision %d", inner);
     const int device = ctxs[0] ? ctxs[0]->device : -1;

@@ -146,6 +146,23 @@ struct Spinor<PLQ_F16> {
             v[4 * k + 3] = {d.x * n, d.y * n};
         }
     }
+    // The stored (normalised) components and the site norm separately: the
+    // hopping kernel projects first and scales the 6 projected components
+    // instead of the 12 loaded ones.
+    __device__ static float load_unscaled(const void *base, size_t stride, size_t e, cx<float> v[12]) {
+        const uint4 *p = static_cast<const uint4 *>(base) + e;
+        const float *nrm = reinterpret_cast<const float *>(static_cast<const uint4 *>(base) + 3 * stride);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 t = ld_nc(p + k * stride);
+            float2 a = h2f(t.x), b = h2f(t.y), c = h2f(t.z), d = h2f(t.w);
+            v[4 * k + 0] = {a.x, a.y};
+            v[4 * k + 1] = {b.x, b.y};
+            v[4 * k + 2] = {c.x, c.y};
+            v[4 * k + 3] = {d.x, d.y};
+        }
+        return ld_nc(nrm + e);
+    }
     __device__ static void store(void *base, size_t stride, size_t e, const cx<float> v[12]) {
         uint4 *p = static_cast<uint4 *>(base) + e;
         float *nrm = reinterpret_cast<float *>(static_cast<uint4 *>(base) + 3 * stride);
@@ -286,11 +303,16 @@ __device__ __forceinline__ void finalize_one(int fin, SolverState *st, const dou
         st->pAp = tot[0];
         st->alpha = st->rho / tot[0];
         if (!isfinite(st->alpha)) { st->flags |= FLAG_NAN; st->stop = 1; }
+        if (st->hist && st->iter < st->hist_cap) st->hist[3 * st->iter] = st->alpha;
         break;
     case FIN_CG_BETA:
         st->rho_new = tot[0];
         st->beta = tot[0] / st->rho;
         st->rho = tot[0];
+        if (st->hist && st->iter < st->hist_cap) {
+            st->hist[3 * st->iter + 1] = st->beta;
+            st->hist[3 * st->iter + 2] = tot[0];
+        }
         st->iter += 1;
         if (!isfinite(tot[0])) { st->flags |= FLAG_NAN; st->stop = 1; }
         else if (tot[0] <= st->stop_r2 || st->iter >= st->maxit) st->stop = 1;

@@ -115,6 +115,20 @@ __device__ __forceinline__ int lex_stride(const Lattice &L, int mu) {
     return mu == 0 ? L.L[1] * L.L[2] * L.L[3] : mu == 1 ? 1 : mu == 2 ? L.L[1] : L.L[1] * L.L[2];
 }
 
+// Neighbour spinor for the projection: FP16 storage returns the normalised
+// components and the site norm (applied to the 6 projected components, not
+// the 12 loaded ones); the other formats return scale 1.
+template <int P>
+__device__ __forceinline__ RealOf<P> load_for_projection(const void *base, size_t stride, size_t e,
+                                                        cx<RealOf<P>> phi[12]) {
+    if constexpr (P == PLQ_F16) {
+        return Spinor<PLQ_F16>::load_unscaled(base, stride, e, phi);
+    } else {
+        Spinor<P>::load(base, stride, e, phi);
+        return RealOf<P>(1);
+    }
+}
+
 // Contribution of direction MU (forward and backward) to the accumulators of
 // RT right-hand sides r0 .. r0+RT-1 of output site i.  Each link is loaded once
 // and applied to all RT neighbour spinors.
@@ -151,12 +165,13 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
 #pragma unroll
         for (int t = 0; t < RT; ++t) {
             cx<T> phi[12];
-            Spinor<P>::load(a.in, stride, (size_t)j * n + r0 + t, phi);
+            T sc = load_for_projection<P>(a.in, stride, (size_t)j * n + r0 + t, phi);
             cx<T> h[6];
             project<MU, SF>(phi, h);
-            if (MU == 0 && flip) {
+            if (MU == 0 && flip) sc = -sc;
+            if (P == PLQ_F16 || (MU == 0 && flip)) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) h[k] = {-h[k].re, -h[k].im};
+                for (int k = 0; k < 6; ++k) h[k] = {sc * h[k].re, sc * h[k].im};
             }
             cx<T> uh[6];
             su3_mul(u, h, uh);
@@ -181,12 +196,13 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
 #pragma unroll
         for (int t = 0; t < RT; ++t) {
             cx<T> phi[12];
-            Spinor<P>::load(a.in, stride, (size_t)j * n + r0 + t, phi);
+            T sc = load_for_projection<P>(a.in, stride, (size_t)j * n + r0 + t, phi);
             cx<T> h[6];
             project<MU, SB>(phi, h);
-            if (MU == 0 && flip) {
+            if (MU == 0 && flip) sc = -sc;
+            if (P == PLQ_F16 || (MU == 0 && flip)) {
 #pragma unroll
-                for (int k = 0; k < 6; ++k) h[k] = {-h[k].re, -h[k].im};
+                for (int k = 0; k < 6; ++k) h[k] = {sc * h[k].re, sc * h[k].im};
             }
             cx<T> uh[6];
             su3_dag_mul(u, h, uh);
@@ -298,6 +314,219 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
     if constexpr (NV > 0) grid_reduce(a.red, racc);
 }
 
+// Multi-RHS variant with the links staged in shared memory.  A block owns
+// blockDim.y sites; its threads first load the 8 links of each of those sites
+// once (rebuilding row 2 of 12-real links once) together with the neighbour
+// indices, then every (site, RHS-tile) thread reads its links from shared
+// memory, where the n/RT threads of a site get them as broadcasts.  This
+// removes the per-RHS link requests that make the L1 the bottleneck of the
+// plain multi-RHS kernel.
+constexpr int kMaxSitesPerBlock = 32;
+
+template <int P, int R, int EPI, bool DAG, int RT>
+__global__ void __launch_bounds__(256) hop_mrhs_kernel(const HopArgs a) {
+    using T = RealOf<P>;
+    __shared__ cx<T> sU[kMaxSitesPerBlock][8][9];
+    __shared__ int sJ[kMaxSitesPerBlock][8];  // neighbour index | flip << 31
+    const int n = a.nrhs;
+    const size_t stride = (size_t)a.lat.Vh * n;
+    constexpr int NV = EPI == EPI_XPAY_NORM ? 1 : 0;
+    RedAcc<1, T> racc;
+    if constexpr (NV > 0) red_init(racc, n);
+    const Lattice &L = a.lat;
+    const char *gbase = static_cast<const char *>(a.gauge);
+    const int S = blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    const int r0 = threadIdx.x * RT;
+    const int plane = L.L[2] * (L.L[1] >> 1);
+    const int zc = a.zc;
+    const int nblk = (L.Vh + S - 1) / S;
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        __syncthreads();  // the previous site block is done with the shared links
+        // stage: (site, direction) pairs
+        for (int q = tid; q < S * 8; q += nthr) {
+            const int k = q >> 3, d = q & 7, mu = d >> 1, back = d & 1;
+            const int li = blk * S + k;
+            if (li >= L.Vh) continue;
+            int i = li;
+            if (zc > 0) {
+                const int per_chunk = L.L[0] * zc * plane;
+                const int c = li / per_chunk;
+                int rem = li - c * per_chunk;
+                const int t = rem / (zc * plane);
+                rem -= t * zc * plane;
+                const int zi = rem / plane;
+                i = (t * L.L[3] + c * zc + zi) * plane + (rem - zi * plane);
+            }
+            const SiteGeom g = site_geom(L, a.out_parity, i);
+            const int st = mu == 0 ? L.L[1] * L.L[2] * L.L[3] : mu == 1 ? 1 : mu == 2 ? L.L[1] : L.L[1] * L.L[2];
+            const int cm = g.c[mu], Lm = L.L[mu];
+            int j;
+            bool flip;
+            if (!back) {
+                j = ((cm == Lm - 1) ? g.lex - (Lm - 1) * st : g.lex + st) >> 1;
+                flip = mu == 0 && cm == Lm - 1 && L.t_bc < 0;
+            } else {
+                j = ((cm == 0) ? g.lex + (Lm - 1) * st : g.lex - st) >> 1;
+                flip = mu == 0 && cm == 0 && L.t_bc < 0;
+            }
+            cx<T> u[3][3];
+            Link<P, R>::load(gbase + (size_t)((back ? 1 - a.out_parity : a.out_parity) * 4 + mu) * a.gblock, L.Vh,
+                             back ? j : i, u);
+#pragma unroll
+            for (int e = 0; e < 9; ++e) sU[k][d][e] = u[e / 3][e % 3];
+            sJ[k][d] = j | (flip ? (int)0x80000000u : 0);
+            if (d == 0) sJ[k][0] |= 0;  // (index of the site itself is not needed)
+        }
+        __syncthreads();
+        const int k = threadIdx.y;
+        const int li = blk * S + k;
+        if (li >= L.Vh) continue;
+        int i = li;
+        if (zc > 0) {
+            const int per_chunk = L.L[0] * zc * plane;
+            const int c = li / per_chunk;
+            int rem = li - c * per_chunk;
+            const int t = rem / (zc * plane);
+            rem -= t * zc * plane;
+            const int zi = rem / plane;
+            i = (t * L.L[3] + c * zc + zi) * plane + (rem - zi * plane);
+        }
+        bool all_frozen = a.st != nullptr;
+#pragma unroll
+        for (int t = 0; t < RT; ++t) all_frozen = all_frozen && a.st[r0 + t].stop;
+        if (all_frozen) continue;
+        cx<T> acc[RT][12];
+#pragma unroll
+        for (int t = 0; t < RT; ++t)
+#pragma unroll
+            for (int e = 0; e < 12; ++e) acc[t][e] = {T(0), T(0)};
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int v = sJ[k][d];
+            const int j = v & 0x7fffffff;
+            const bool flip = v < 0;
+            const int mu = d >> 1;
+#pragma unroll
+            for (int t = 0; t < RT; ++t) {
+                cx<T> phi[12];
+                T sc = load_for_projection<P>(a.in, stride, (size_t)j * n + r0 + t, phi);
+                if (flip) sc = -sc;
+                cx<T> hh[6], uh[6];
+                // project, scale, multiply by U (forward) or U^dagger (backward), rebuild
+#define PLQ_DIR(MU)                                                                        \
+    if (mu == MU) {                                                                        \
+        constexpr int SF = DAG ? +1 : -1;                                                  \
+        if ((d & 1) == 0) project<MU, SF>(phi, hh);                                        \
+        else project<MU, -SF>(phi, hh);                                                    \
+    }
+                PLQ_DIR(0) PLQ_DIR(1) PLQ_DIR(2) PLQ_DIR(3)
+#undef PLQ_DIR
+#pragma unroll
+                for (int e = 0; e < 6; ++e) hh[e] = {sc * hh[e].re, sc * hh[e].im};
+                const cx<T>(*su)[9] = &sU[k][d];
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        cx<T> z{0, 0};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            if ((d & 1) == 0) z = cfma((*su)[3 * r + c], hh[3 * s + c], z);
+                            else z = cfma_conj((*su)[3 * c + r], hh[3 * s + c], z);
+                        }
+                        uh[3 * s + r] = z;
+                    }
+#define PLQ_REC(MU)                                                                        \
+    if (mu == MU) {                                                                        \
+        constexpr int SF = DAG ? +1 : -1;                                                  \
+        if ((d & 1) == 0) reconstruct<MU, SF>(acc[t], uh);                                 \
+        else reconstruct<MU, -SF>(acc[t], uh);                                             \
+    }
+                PLQ_REC(0) PLQ_REC(1) PLQ_REC(2) PLQ_REC(3)
+#undef PLQ_REC
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < RT; ++t) {
+            const int rr = r0 + t;
+            if (a.st != nullptr && a.st[rr].stop) continue;
+            const long long idx = (long long)i * n + rr;
+            if (a.nu_h != 0.0 || a.scale_h != 1.0) twist12(acc[t], (T)a.nu_h, (T)a.scale_h);
+            if constexpr (EPI != EPI_PLAIN) {
+                cx<T> xv[12];
+                Spinor<P>::load(a.x, stride, (size_t)idx, xv);
+                if (a.nu_x != 0.0) twist12(xv, (T)a.nu_x, T(1));
+                const T s = (T)a.a;
+#pragma unroll
+                for (int e = 0; e < 12; ++e) {
+                    acc[t][e].re = fma(s, acc[t][e].re, xv[e].re);
+                    acc[t][e].im = fma(s, acc[t][e].im, xv[e].im);
+                }
+                if constexpr (EPI == EPI_XPAY_NORM) {
+                    T s0 = 0;
+#pragma unroll
+                    for (int e = 0; e < 12; ++e) s0 += acc[t][e].re * acc[t][e].re + acc[t][e].im * acc[t][e].im;
+                    racc.add(0, rr, s0);
+                }
+            }
+            Spinor<P>::store(a.out, stride, (size_t)idx, acc[t]);
+        }
+    }
+    if constexpr (NV > 0) grid_reduce(a.red, racc);
+}
+
+template <int P, int R, int EPI, bool DAG, int RT>
+plq_status launch_mrhs_t(const HopArgs &a, cudaStream_t s, int block) {
+    if (a.block > 0) block = a.block;
+    if (block <= 0 || block > 256) block = 128;
+    const int n = a.nrhs;
+    const int tiles = n / RT;
+    int spb = block / tiles > 0 ? block / tiles : 1;
+    if (spb > kMaxSitesPerBlock) spb = kMaxSitesPerBlock;
+    for (int q = spb; q >= 1; --q)
+        if ((q * tiles) % 32 == 0) {
+            spb = q;
+            break;
+        }
+    const int threads = tiles * spb;
+    static int per_sm[257] = {0};
+    auto kern = hop_mrhs_kernel<P, R, EPI, DAG, RT>;
+    if (per_sm[threads] == 0) {
+        int nb = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0);
+        if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(hop_mrhs)");
+        per_sm[threads] = nb > 0 ? nb : 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = ((long long)a.lat.Vh + spb - 1) / spb;
+    long long cap = (long long)per_sm[threads] * sms;
+    if (EPI >= EPI_XPAY_NORM && cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
+    const int grid = (int)(want < cap ? want : cap);
+    if (grid <= 0) return PLQ_OK;
+    kern<<<grid, dim3(tiles, spb), 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "hop_mrhs_kernel launch");
+    return PLQ_OK;
+}
+
+template <int P, int R, int RT>
+plq_status dispatch_mrhs(const HopArgs &a, int epi, cudaStream_t s, int block) {
+    switch (epi) {
+    case EPI_PLAIN:
+        return a.dagger ? launch_mrhs_t<P, R, EPI_PLAIN, true, RT>(a, s, block)
+                        : launch_mrhs_t<P, R, EPI_PLAIN, false, RT>(a, s, block);
+    case EPI_XPAY:
+        return a.dagger ? launch_mrhs_t<P, R, EPI_XPAY, true, RT>(a, s, block)
+                        : launch_mrhs_t<P, R, EPI_XPAY, false, RT>(a, s, block);
+    default:
+        return a.dagger ? launch_mrhs_t<P, R, EPI_XPAY_NORM, true, RT>(a, s, block)
+                        : launch_mrhs_t<P, R, EPI_XPAY_NORM, false, RT>(a, s, block);
+    }
+}
+
 // Launch helper: grid = min(work blocks, resident blocks on all SMs).
 template <int P, int R, int EPI, bool DAG, bool TBL = false, int RT = 1>
 plq_status launch_hop_t(const HopArgs &a, cudaStream_t s, int block) {
@@ -359,6 +588,10 @@ plq_status dispatch_hop(const HopArgs &a, int epi, cudaStream_t s, int block) {
     // formats and the epilogues of operator applications and CG; the
     // neighbour-table variants for the plain and xpay epilogues.
     if constexpr (P != PLQ_F64) {
+        if (a.smem_links && a.nrhs > 1 && a.site_begin == 0 && a.site_end < 0 && epi <= EPI_XPAY_NORM) {
+            if (a.rhs_tile == 2 && a.nrhs % 2 == 0) return dispatch_mrhs<P, R, 2>(a, epi, s, block);
+            return dispatch_mrhs<P, R, 1>(a, epi, s, block);
+        }
         if (a.rhs_tile > 1 && a.nrhs % a.rhs_tile == 0 && epi <= EPI_XPAY_NORM) {
             if (a.rhs_tile == 2) return dispatch_tiled<P, R, 2>(a, epi, s, block);
             if (a.rhs_tile == 4) return dispatch_tiled<P, R, 4>(a, epi, s, block);

@@ -72,6 +72,12 @@ struct SolverState {
     int iter;         // iterations completed
     int flags;        // bit 0 NaN, bit 1 breakdown
     int maxit;        // stop once iter reaches this
+    // Optional per-iteration record of the CG coefficients (EigCG builds its
+    // Lanczos matrix from them): hist[3*j + {0, 1, 2}] = alpha_j, beta_j,
+    // |r_{j+1}|^2 for iteration j < hist_cap.
+    double *hist;
+    int hist_cap;
+    int pad2;
 };
 
 enum { FLAG_NAN = 1, FLAG_BREAKDOWN = 2 };
@@ -103,6 +109,7 @@ struct TuneEntry {
     int index_mode = 0;  // 0 inline coordinates, 1 neighbour table
     int rhs_tile = 1;    // right-hand sides per thread
     int zc = 0;          // z-chunk site order (0 = natural)
+    int smem_links = 0;  // multi-RHS links staged in shared memory
     float us = 0.f;
 };
 
@@ -132,6 +139,10 @@ struct Ctx {
 
 plq_status ensure_work(Ctx *c, size_t bytes);
 plq_status ensure_nbr_tables(Ctx *c);
+// ||b - M x||^2 and ||b||^2 of packed full FP64 fields (Wilson operator, FP64;
+// uses the context's workspace and synchronises the stream)
+plq_status wilson_residual64(struct plq_ctx *c, double kappa, const void *x, const void *b, double *r2, double *b2,
+                             cudaStream_t s);
 plq_status ensure_stage(Ctx *c, size_t bytes);
 plq_status ensure_pipeline(Ctx *c);
 
@@ -176,6 +187,7 @@ struct HopArgs {
     double nu_x = 0.0, nu_h = 0.0, scale_h = 1.0;
     int site_begin = 0;   // output sites [site_begin, site_end) of the parity;
     int site_end = -1;    // -1: up to Vh
+    int smem_links = 0;   // multi-RHS: stage each block's links in shared memory
 };
 
 // Launch the hopping kernel for (prec, link reals, epilogue).  block = 0 picks

@@ -49,13 +49,14 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         char k[600];
-        int block = 0, mode = 0, tile = 1, zc = 0;
+        int block = 0, mode = 0, tile = 1, zc = 0, sm = 0;
         float us = 0;
-        if (sscanf(line, "%599s %d %d %d %d %f", k, &block, &mode, &tile, &zc, &us) == 6 && key == k) {
+        if (sscanf(line, "%599s %d %d %d %d %d %f", k, &block, &mode, &tile, &zc, &sm, &us) == 7 && key == k) {
             e->block = block;
             e->index_mode = mode;
             e->rhs_tile = tile;
             e->zc = zc;
+            e->smem_links = sm;
             e->us = us;
             found = true;  // last entry wins
         }
@@ -67,7 +68,8 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
 void cache_store(const char *path, const std::string &key, const TuneEntry &e) {
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %.3f\n", key.c_str(), e.block, e.index_mode, e.rhs_tile, e.zc, e.us);
+    fprintf(f, "%s %d %d %d %d %d %.3f\n", key.c_str(), e.block, e.index_mode, e.rhs_tile, e.zc, e.smem_links,
+            e.us);
     fclose(f);
 }
 
@@ -92,6 +94,7 @@ void apply_tune(const Ctx *c, int prec, int nrhs, HopArgs &a) {
     a.nbr = (e.index_mode == 1) ? c->nbr[a.out_parity] : nullptr;
     a.rhs_tile = (e.rhs_tile > 1 && nrhs % e.rhs_tile == 0) ? e.rhs_tile : 1;
     a.zc = (e.zc > 0 && c->lat.L[3] % e.zc == 0) ? e.zc : 0;
+    a.smem_links = nrhs > 1 ? e.smem_links : 0;
 }
 
 }  // namespace plq
@@ -116,6 +119,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
             res->index_mode = best.index_mode;
             res->rhs_tile = best.rhs_tile;
             res->z_chunk = best.zc;
+            res->smem_links = best.smem_links;
             res->us_per_launch = best.us;
             res->from_cache = 1;
         }
@@ -143,7 +147,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
     const int reps = 10;
     // candidates: index mode x block size, plus right-hand-side tiles for nrhs > 1
     struct Cand {
-        int mode, tile, zc;
+        int mode, tile, zc, smem;
     };
     Cand cands[24];
     int nc = 0;
@@ -153,10 +157,12 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
         if (z < Lz && Lz % z == 0) zcs[nz++] = z;
     for (int zi = 0; zi < nz; ++zi) {
         const int z = zcs[zi];
-        cands[nc++] = {0, 1, z};
-        if (z == 0) cands[nc++] = {1, 1, 0};
-        if (prec != PLQ_F64 && nrhs % 2 == 0) cands[nc++] = {0, 2, z};
-        if (prec != PLQ_F64 && nrhs % 4 == 0) cands[nc++] = {0, 4, z};
+        cands[nc++] = {0, 1, z, 0};
+        if (z == 0) cands[nc++] = {1, 1, 0, 0};
+        if (prec != PLQ_F64 && nrhs % 2 == 0) cands[nc++] = {0, 2, z, 0};
+        if (prec != PLQ_F64 && nrhs % 4 == 0) cands[nc++] = {0, 4, z, 0};
+        if (prec != PLQ_F64 && nrhs > 1) cands[nc++] = {0, 1, z, 1};
+        if (prec != PLQ_F64 && nrhs > 1 && nrhs % 2 == 0) cands[nc++] = {0, 2, z, 1};
     }
     for (int ci = 0; ci < nc && st == PLQ_OK; ++ci) {
         const int mode = cands[ci].mode;
@@ -173,6 +179,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
             a.nbr = mode ? c->nbr[0] : nullptr;
             a.rhs_tile = cands[ci].tile;
             a.zc = cands[ci].zc;
+            a.smem_links = cands[ci].smem;
             for (int w = 0; w < 2 && st == PLQ_OK; ++w) st = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
             cudaEventRecord(e0, s);
             for (int r = 0; r < reps && st == PLQ_OK; ++r) st = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
@@ -193,6 +200,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
                 best.index_mode = mode;
                 best.rhs_tile = cands[ci].tile;
                 best.zc = cands[ci].zc;
+                best.smem_links = cands[ci].smem;
             }
         }
     }
@@ -209,6 +217,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
         res->index_mode = best.index_mode;
         res->rhs_tile = best.rhs_tile;
         res->z_chunk = best.zc;
+        res->smem_links = best.smem_links;
         res->us_per_launch = best.us;
         res->from_cache = 0;
         res->candidates = tried;
@@ -217,7 +226,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
 }
 
 extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, int index_mode, int rhs_tile,
-                                     int z_chunk) {
+                                     int z_chunk, int smem_links) {
     if (!c) return set_error(PLQ_ERR_ARG, "null context");
     if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
     if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
@@ -234,5 +243,6 @@ extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, 
     c->tune[prec][nrhs].index_mode = index_mode;
     c->tune[prec][nrhs].rhs_tile = rhs_tile;
     c->tune[prec][nrhs].zc = z_chunk;
+    c->tune[prec][nrhs].smem_links = smem_links ? 1 : 0;
     return PLQ_OK;
 }

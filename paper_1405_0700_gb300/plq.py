@@ -54,6 +54,7 @@ class TuneResult(ctypes.Structure):
         ("index_mode", ctypes.c_int),
         ("rhs_tile", ctypes.c_int),
         ("z_chunk", ctypes.c_int),
+        ("smem_links", ctypes.c_int),
         ("us_per_launch", ctypes.c_double),
         ("from_cache", ctypes.c_int),
         ("candidates", ctypes.c_int),
@@ -118,10 +119,15 @@ SIGNATURES = {
     "plq_theta_bytes": (_c_size, [_vp, _c_int]),
     "plq_hopping_eo_theta": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _c_int, _vp]),
     "plq_link_spinor_stream": (_c_int, [_c_int, ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _c_int, _vp]),
+    "plq_eigcg_create": (_c_int, [_vp, _c_int, _c_int, _c_int, ctypes.POINTER(_vp)]),
+    "plq_eigcg_destroy": (_c_int, [_vp]),
+    "plq_eigcg_vectors": (_c_int, [_vp]),
+    "plq_eigcg_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams), _c_int,
+                                 ctypes.POINTER(SolveInfo), _vp]),
     "plq_measure_fma_rate": (_c_int, [_c_int, _c_int, ctypes.POINTER(ctypes.c_double)]),
     "plq_schur_apply_noalloc": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, _c_int, _vp]),
     "plq_autotune": (_c_int, [_vp, _c_int, _c_int, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
-    "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int]),
+    "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int]),
 }
 
 _lib = None
@@ -327,8 +333,8 @@ class Context:
         check(lib().plq_autotune(self._h, prec_of(prec), nrhs, path, ctypes.byref(r)))
         return r.as_dict()
 
-    def set_launch(self, prec, nrhs=1, block=0, index_mode=0, rhs_tile=1, z_chunk=0):
-        check(lib().plq_set_launch(self._h, prec_of(prec), nrhs, block, index_mode, rhs_tile, z_chunk))
+    def set_launch(self, prec, nrhs=1, block=0, index_mode=0, rhs_tile=1, z_chunk=0, smem_links=0):
+        check(lib().plq_set_launch(self._h, prec_of(prec), nrhs, block, index_mode, rhs_tile, z_chunk, smem_links))
 
     # ------------------------------------------------------------ solvers
     def _solve(self, fn, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every, stream, raise_on_error,
@@ -340,7 +346,7 @@ class Context:
             check(st, info)
         return info
 
-    def cg_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
+    def cg_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0, use_x0=False,
                  check_every=16, stream=None, raise_on_error=True, mu=0.0):
         """CG on the even-odd normal equations; x, b packed full FP64 fields (mu: twisted mass)."""
         return self._solve(lib().plq_cg_solve, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every,
@@ -355,25 +361,25 @@ class Context:
             check(st, list(infos))
         return list(infos)
 
-    def cg_solve_multi(self, x, b, kappa, nrhs, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
+    def cg_solve_multi(self, x, b, kappa, nrhs, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0, use_x0=False,
                        check_every=16, stream=None, raise_on_error=True):
         """CG for nrhs interleaved right-hand sides (links loaded once per operator application)."""
         return self._solve_multi(lib().plq_cg_solve_multi, x, b, kappa, nrhs, tol, maxit, inner_prec, delta, use_x0,
                                  check_every, stream, raise_on_error)
 
-    def bicgstab_solve_multi(self, x, b, kappa, nrhs, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1,
+    def bicgstab_solve_multi(self, x, b, kappa, nrhs, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0,
                              use_x0=False, check_every=16, stream=None, raise_on_error=True):
         return self._solve_multi(lib().plq_bicgstab_solve_multi, x, b, kappa, nrhs, tol, maxit, inner_prec, delta,
                                  use_x0, check_every, stream, raise_on_error)
 
-    def bicgstab_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
+    def bicgstab_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0, use_x0=False,
                        check_every=16, stream=None, raise_on_error=True, mu=0.0):
         """BiCGstab on the even-odd Schur system; x, b packed full FP64 fields (mu: twisted mass)."""
         return self._solve(lib().plq_bicgstab_solve, x, b, kappa, tol, maxit, inner_prec, delta, use_x0,
                            check_every, stream, raise_on_error, mu)
 
 
-def cg_solve_batched(ctxs, xs, bs, kappas, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.1, use_x0=False,
+def cg_solve_batched(ctxs, xs, bs, kappas, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0, use_x0=False,
                      stream=None, raise_on_error=True):
     """One persistent launch solving len(ctxs) independent systems (see plq_cg_solve_batched)."""
     n = len(ctxs)
@@ -388,6 +394,40 @@ def cg_solve_batched(ctxs, xs, bs, kappas, tol=1e-10, maxit=20000, inner_prec=F6
     if raise_on_error:
         check(st, (list(infos), bi))
     return list(infos), bi.as_dict()
+
+
+class EigCG:
+    """Incremental EigCG deflation on a context (see plq_eigcg_create / plq_eigcg_solve)."""
+
+    def __init__(self, ctx, nev=10, m=60, max_vectors=300):
+        h = _vp()
+        check(lib().plq_eigcg_create(ctx.handle, nev, m, max_vectors, ctypes.byref(h)))
+        self._h = h
+        self.ctx = ctx
+
+    @property
+    def vectors(self):
+        return int(lib().plq_eigcg_vectors(self._h))
+
+    def solve(self, x, b, kappa, tol=1e-8, maxit=20000, accumulate=True, stream=None, raise_on_error=True):
+        p = SolverParams(tol, maxit, F64, 0.0, 0, 16, 0.0)
+        info = SolveInfo()
+        st = lib().plq_eigcg_solve(self._h, _ptr(x), _ptr(b), float(kappa), ctypes.byref(p), int(bool(accumulate)),
+                                   ctypes.byref(info), _stream(stream))
+        if raise_on_error:
+            check(st, info)
+        return info
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().plq_eigcg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def link_spinor_stream(mode, nsites, U, phi, psi, index=None, pointers=None, prec=F32, stream=None):

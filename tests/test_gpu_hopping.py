@@ -116,9 +116,9 @@ def test_multi_rhs(nrhs, prec, reals):
         assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
 
 
-@pytest.mark.parametrize("tile,zc", [(2, 0), (4, 0), (1, 2), (2, 4)])
+@pytest.mark.parametrize("tile,zc,sm", [(2, 0, 0), (4, 0, 0), (1, 2, 0), (2, 4, 0), (1, 0, 1), (2, 4, 1)])
 @pytest.mark.parametrize("prec,reals", [(F32, 18), (F32, 12), (F16, 12), (F16, 18)])
-def test_multi_rhs_tiles(tile, zc, prec, reals):
+def test_multi_rhs_tiles(tile, zc, sm, prec, reals):
     # each thread applies every link it loads to `tile` right-hand sides; zc walks the
     # sites in z-chunks
     dims = (6, 4, 2, 8)
@@ -127,7 +127,7 @@ def test_multi_rhs_tiles(tile, zc, prec, reals):
     phis = np.stack([S.gaussian_spinor(dims, 200 + r) for r in range(nrhs)])
     with Context(dims) as ctx:
         ctx.gauge_upload(U, reals, prec)
-        ctx.set_launch(prec, nrhs, 96, 0, tile, zc)
+        ctx.set_launch(prec, nrhs, 96, 0, tile, zc, sm)
         got = gpu_hopping_full(ctx, phis, prec, nrhs).reshape(phis.shape)
     for r in range(nrhs):
         assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r

@@ -125,7 +125,7 @@ def test_missing_inner_gauge_copy():
         assert e.value.status == plq.PLQ_ERR_STATE
 
 
-def run_multi(method, dims, eps, seed, kappa, inner, sources, tile=1, **kw):
+def run_multi(method, dims, eps, seed, kappa, inner, sources, tile=1, sm=0, **kw):
     U = S.gauge_field(dims, eps, seed)
     n = len(sources)
     b = np.stack(sources)
@@ -133,7 +133,7 @@ def run_multi(method, dims, eps, seed, kappa, inner, sources, tile=1, **kw):
         ctx.gauge_upload(U, 18, F64)
         if inner != F64:
             ctx.gauge_upload(U, 12, inner)
-            ctx.set_launch(inner, n, 0, 0, tile)
+            ctx.set_launch(inner, n, 0, 0, tile, 0, sm)
         bd = ctx.to_device(b, F64, n)
         x = ctx.empty_full(F64, n)
         fn = ctx.cg_solve_multi if method == "cg" else ctx.bicgstab_solve_multi
@@ -158,12 +158,12 @@ def test_multi_rhs_point_sources(method, inner):
         assert abs(infos[r].true_rel_residual - res) < 1e-11
 
 
-@pytest.mark.parametrize("tile", [2, 4])
-def test_multi_rhs_cg_with_rhs_tiles(tile):
+@pytest.mark.parametrize("tile,sm", [(2, 0), (4, 0), (1, 1), (2, 1)])
+def test_multi_rhs_cg_with_rhs_tiles(tile, sm):
     dims = (8, 4, 4, 8)
     kappa = 0.12
     srcs = [S.point_source(dims, s, c) for s in range(4) for c in range(3)]
-    U, b, x, infos = run_multi("cg", dims, 0.3, 9, kappa, F32, srcs, tile=tile)
+    U, b, x, infos = run_multi("cg", dims, 0.3, 9, kappa, F32, srcs, tile=tile, sm=sm)
     for r in range(12):
         assert oracle_residual(U, b[r], x[r], kappa) <= 1e-10
 

@@ -221,8 +221,8 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
 // Threads are arranged as (n / RT right-hand-side tiles) x (sites): the
 // threads of one site are adjacent and share its link loads through L1, and
 // each thread applies every link it loads to RT right-hand sides.
-template <int P, int R, int EPI, bool DAG, bool TBL, int RT = 1>
-__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
+template <int P, int R, int EPI, bool DAG, bool TBL, int RT>
+__device__ __forceinline__ void hop_body(const HopArgs &a) {
     using T = RealOf<P>;
     const int n = a.nrhs;
     const long long total = (long long)a.lat.Vh * n;
@@ -312,6 +312,33 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
         }
     }
     if constexpr (NV > 0) grid_reduce(a.red, racc);
+}
+
+// Register budget of the one-RHS kernels (0: the compiler's choice under a
+// 256-thread launch bound).  Left alone the compiler hoists the loads of
+// several directions and takes ~140 registers (FP32, 18-real links), which
+// leaves 3 blocks of 128 threads per SM; a cap trades part of that hoisting
+// for resident warps, i.e. more bytes in flight per SM.  The values are the
+// fastest of a sweep (64..112) on the 32^3x64 half-application: 80 for FP32
+// with 18-real links, 72 for the other FP32/FP16 formats, 96 for the
+// epilogue kernels of the solvers.  FP64 is bound by its arithmetic and
+// runs uncapped, as do the neighbour-table variants (~72 registers anyway)
+// and the RHS-tiled kernels, whose tiles live in registers.
+template <int P, int R, int EPI, bool TBL, int RT>
+constexpr int hop_reg_cap() {
+    if (RT != 1 || TBL || P == PLQ_F64) return 0;
+    if (EPI != EPI_PLAIN) return 96;
+    return (P == PLQ_F32 && R == 18) ? 80 : 72;
+}
+
+template <int P, int R, int EPI, bool DAG, bool TBL, int RT = 1>
+__global__ void __launch_bounds__(256) hop_kernel(const HopArgs a) {
+    hop_body<P, R, EPI, DAG, TBL, RT>(a);
+}
+
+template <int P, int R, int EPI, bool DAG, bool TBL, int RT, int NREG>
+__global__ void __maxnreg__(NREG) hop_kernel_capped(const HopArgs a) {
+    hop_body<P, R, EPI, DAG, TBL, RT>(a);
 }
 
 // Multi-RHS variant with the links staged in shared memory.  A block owns
@@ -544,7 +571,11 @@ plq_status launch_hop_t(const HopArgs &a, cudaStream_t s, int block) {
         }
     const int threads = tiles * spb;
     static int per_sm[257] = {0};
-    auto kern = hop_kernel<P, R, EPI, DAG, TBL, RT>;
+    constexpr int nreg = hop_reg_cap<P, R, EPI, TBL, RT>();
+    auto kern = [] {
+        if constexpr (nreg > 0) return hop_kernel_capped<P, R, EPI, DAG, TBL, RT, (nreg > 0 ? nreg : 255)>;
+        else return hop_kernel<P, R, EPI, DAG, TBL, RT>;
+    }();
     if (per_sm[threads] == 0) {
         int nb = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0);

@@ -42,11 +42,11 @@ FLOP_PER_SITE = 1320
 # compulsory bytes per output site of a half-application: the input-parity
 # spinor, the output spinor and the 8 links touching the site, each once
 COMPULSORY = {("f64", 18): 1536, ("f64", 12): 1152, ("f32", 18): 768, ("f32", 12): 576,
-              ("f16", 18): 392, ("f16", 12): 296}
+              ("f16", 18): 392, ("f16", 12): 296, ("df64", 18): 1536}
 # literature convention without reuse: 8 neighbour spinors + 8 links + 1 output
 NO_REUSE = {("f64", 18): 8 * 192 + 8 * 144 + 192, ("f32", 18): 8 * 96 + 8 * 72 + 96,
             ("f32", 12): 8 * 96 + 8 * 48 + 96, ("f16", 12): 8 * 52 + 8 * 24 + 52,
-            ("f16", 18): 8 * 52 + 8 * 36 + 52, ("f64", 12): 8 * 192 + 8 * 96 + 192}
+            ("f16", 18): 8 * 52 + 8 * 36 + 52, ("f64", 12): 8 * 192 + 8 * 96 + 192, ("df64", 18): 8 * 192 + 8 * 144 + 192}
 HOP_DIMS = (64, 32, 32, 32)
 CG_DIMS = (48, 24, 24, 24)
 
@@ -243,7 +243,7 @@ def roofline_entry(ms, vh, prec_name, reals, peak_gbs):
 
 
 def cg_section(torch, local_rank, quick):
-    from paper_1405_0700_gb300 import F16, F32, F64, Context
+    from paper_1405_0700_gb300 import DF64, F16, F32, F64, Context
 
     dims = CG_DIMS if not quick else (16, 8, 8, 8)
     kappa = 0.120
@@ -254,17 +254,23 @@ def cg_section(torch, local_rank, quick):
         ctx.gauge_upload(U, 18, F64)
         ctx.gauge_upload(U, 12, F32)
         ctx.gauge_upload(U, 12, F16)
+        ctx.gauge_upload(U, 18, DF64)
         bd = ctx.to_device(b, F64)
         x = ctx.empty_full(F64)
         runs = {}
-        for name, method, inner in [("cg_f64", "cg", F64), ("cg_mixed_f32", "cg", F32),
-                                    ("cg_mixed_f16", "cg", F16), ("bicgstab_f64", "bicgstab", F64),
-                                    ("bicgstab_mixed_f32", "bicgstab", F32)]:
+        # *_dfres: the reliable-update residuals in float-float arithmetic (the
+        # returned x is still checked with the FP64 operator)
+        for name, method, inner, rp in [("cg_f64", "cg", F64, F64), ("cg_mixed_f32", "cg", F32, F64),
+                                        ("cg_mixed_f16", "cg", F16, F64), ("cg_mixed_f32_dfres", "cg", F32, DF64),
+                                        ("cg_mixed_f16_dfres", "cg", F16, DF64),
+                                        ("bicgstab_f64", "bicgstab", F64, F64),
+                                        ("bicgstab_mixed_f32", "bicgstab", F32, F64),
+                                        ("bicgstab_mixed_f32_dfres", "bicgstab", F32, DF64)]:
             fn = ctx.cg_solve if method == "cg" else ctx.bicgstab_solve
-            fn(x, bd, kappa, tol=1e-10, inner_prec=inner, raise_on_error=False)  # warm (graphs, workspace)
+            fn(x, bd, kappa, tol=1e-10, inner_prec=inner, raise_on_error=False, residual_prec=rp)  # warm
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            info = fn(x, bd, kappa, tol=1e-10, inner_prec=inner, raise_on_error=False)
+            info = fn(x, bd, kappa, tol=1e-10, inner_prec=inner, raise_on_error=False, residual_prec=rp)
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
             runs[name] = {"seconds": el, "iterations": info.iterations, "reliable_updates": info.n_reliable,
@@ -288,12 +294,13 @@ def cg_section(torch, local_rank, quick):
     f64 = runs["cg_f64"]["seconds"]
     out["speedup_mixed_f32_vs_f64"] = f64 / runs["cg_mixed_f32"]["seconds"]
     out["speedup_mixed_f16_vs_f64"] = f64 / runs["cg_mixed_f16"]["seconds"]
+    out["speedup_mixed_f16_dfres_vs_f64"] = f64 / runs["cg_mixed_f16_dfres"]["seconds"]
     return out
 
 
 def propagator_section(torch, local_rank, quick):
     """12 point sources (spin x colour at the origin): multi-RHS operator and batched mixed CG."""
-    from paper_1405_0700_gb300 import F16, F32, F64, Context
+    from paper_1405_0700_gb300 import DF64, F16, F32, F64, Context
 
     dims = (96, 48, 48, 48) if not quick else (16, 8, 8, 8)
     kappa, eps, seed, n = 0.121, 0.25, 4, 12
@@ -358,6 +365,20 @@ def propagator_section(torch, local_rank, quick):
             "status": [i.status for i in infos]}
         log(f"[bench] batched CG x{n}: {el:.2f}s, it={infos[0].iterations}, "
             f"res<={out['batched_cg_mixed_f32']['max_true_rel_residual']:.2e}")
+        # the same with the reliable-update residuals in float-float arithmetic
+        ctx.gauge_upload(U, 18, DF64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = ctx.cg_solve_multi(x, bd, kappa, n, tol=1e-10, inner_prec=F32, maxit=3000, raise_on_error=False,
+                                   residual_prec=DF64)
+        torch.cuda.synchronize()
+        el_df = time.perf_counter() - t0
+        out["batched_cg_mixed_f32_dfres"] = {
+            "seconds": el_df, "seconds_per_rhs": el_df / n,
+            "iterations": [i.iterations for i in infos], "reliable_updates": infos[0].n_reliable,
+            "max_true_rel_residual": max(i.true_rel_residual for i in infos),
+            "status": [i.status for i in infos]}
+        log(f"[bench] batched CG x{n}, float-float residuals: {el_df:.2f}s")
         # the same right-hand sides one at a time (single-RHS solver, same inner precision)
         singles = []
         for r in range(n if not quick else 2):
@@ -393,7 +414,7 @@ def operator_only(args, torch, local_rank):
     peak, _ = peaks()
     with Context(dims, device=local_rank) as ctx:
         ctx.gauge_upload(U, args.links, prec)
-        tuned = ctx.autotune(prec, n) if args.tune else None
+        tuned = ctx.autotune(prec, n) if args.tune and args.prec != "df64" else None
         if args.launch:
             vals = [int(v) for v in args.launch.split(",")] + [0]
             blk, mode, tile, zc, sm = vals[:5]
@@ -414,9 +435,9 @@ def operator_only(args, torch, local_rank):
             e_.record()
             torch.cuda.synchronize()
             ms = s_.elapsed_time(e_) / args.steps
-    link_b = {("f64", 18): 144, ("f64", 12): 96, ("f32", 18): 72, ("f32", 12): 48, ("f16", 18): 36,
+    link_b = {("f64", 18): 144, ("df64", 18): 144, ("f64", 12): 96, ("f32", 18): 72, ("f32", 12): 48, ("f16", 18): 36,
               ("f16", 12): 24}[(args.prec, args.links)]
-    sp = {"f64": 192, "f32": 96, "f16": 52}[args.prec]
+    sp = {"f64": 192, "df64": 192, "f32": 96, "f16": 52}[args.prec]
     per = 2 * sp + 8 * link_b / n
     gbs = per * vh * n / (ms * 1e-3) / 1e9
     print(json.dumps({"workload": "operator", "lattice": args.lattice or "32x32x32x64", "prec": args.prec,
@@ -534,7 +555,7 @@ def main():
     ap.add_argument("--source-hash", action="store_true", help="print the hash of the headline kernel's sources")
     ap.add_argument("--workload", default="hop", choices=["hop", "propagator", "operator", "eigcg", "batch"],
                     help="hop: the headline operator line (default); propagator: 48^3x96 with 12 point sources")
-    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"])
+    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "df64"])
     ap.add_argument("--links", type=int, default=18, choices=[18, 12])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--tune", action="store_true", help="operator workload: autotune the launch first")
@@ -556,7 +577,7 @@ def main():
 
     import torch
 
-    from paper_1405_0700_gb300 import F16, F32, F64, Context, lib
+    from paper_1405_0700_gb300 import DF64, F16, F32, F64, Context, lib
 
     torch.cuda.set_device(local_rank)
     lib()
@@ -641,9 +662,9 @@ def main():
     # ---- every storage format
     variants = {}
     for pname, prec, reals in [("f32", F32, 18), ("f32", F32, 12), ("f16", F16, 12), ("f16", F16, 18),
-                               ("f64", F64, 18), ("f64", F64, 12)]:
+                               ("f64", F64, 18), ("f64", F64, 12), ("df64", DF64, 18)]:
         ctx.gauge_upload(U, reals, prec)
-        tuned_v = ctx.autotune(prec, 1)
+        tuned_v = ctx.autotune(prec, 1) if prec != DF64 else None
         fv = ctx.to_device(phi, prec)
         _, ov = ctx.halves(fv, prec)
         outv = ctx.empty_half(prec)

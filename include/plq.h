@@ -44,6 +44,9 @@
  *     PLQ_F16:  3 planes of 8 IEEE binary16 values (4 complex), followed by a
  *               float plane of per-site norms n = max |real or imaginary
  *               component|; stored halves are component / n    52 B per site
+ *     PLQ_DF64: the PLQ_F32 half field of the high parts followed by the
+ *               PLQ_F32 half field of the low parts of every real,
+ *               value = hi + lo (float-float)               192 B per site
  *   A full field is the even half followed by the odd half.
  *   plq_field_bytes() gives the byte size of one half field.
  *
@@ -93,8 +96,15 @@ enum {
 };
 
 /* Storage precisions of packed fields.  PLQ_F32 and PLQ_F16 compute in FP32;
- * PLQ_F64 computes in FP64. */
-enum { PLQ_F64 = 0, PLQ_F32 = 1, PLQ_F16 = 2 };
+ * PLQ_F64 computes in FP64.  PLQ_DF64 stores every real as an unevaluated sum
+ * of two floats (hi = rn(d), lo = rn(d - hi): about 48 significant bits, the
+ * exponent range of FP32) and computes in float-float arithmetic built from
+ * the error-free TwoSum and FMA-based TwoProduct; it gives FP64-level
+ * accuracy (relative error ~1e-14) at FP32 instruction rates.  PLQ_DF64 is
+ * accepted by plq_field_bytes, plq_gauge_upload (18 reals), plq_pack_spinor,
+ * plq_unpack_spinor and plq_hopping_eo, and as residual_prec of the solvers;
+ * every other entry point returns PLQ_ERR_ARG for it. */
+enum { PLQ_F64 = 0, PLQ_F32 = 1, PLQ_F16 = 2, PLQ_DF64 = 3 };
 
 /* Maximum number of right-hand sides of the multi-RHS operator (one link load
  * serves all of them; 12 = the spin x colour columns of a point source). */
@@ -115,6 +125,11 @@ typedef struct {
     int check_every;   /* inner iterations per host convergence poll, default 16           */
     double mu;         /* twisted mass: solve M_tm = 1 - kappa H + 2 i kappa mu gamma5
                           (0: the Wilson operator M)                                        */
+    int residual_prec; /* arithmetic of the reliable-update residuals s = bhat - Mhat x of a
+                          mixed-precision solve: PLQ_F64 (default) or PLQ_DF64 (needs the
+                          PLQ_DF64 gauge copy).  The residual of the returned x is always
+                          computed in FP64.  Used by plq_cg_solve(_multi) and
+                          plq_bicgstab_solve(_multi); other solvers ignore it.               */
 } plq_solver_params;
 
 /* Per-solve report. */

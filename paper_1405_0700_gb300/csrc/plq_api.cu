@@ -171,6 +171,7 @@ plq_status plq_finalize(plq_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &g : c->gauge)
         if (g.ptr) cudaFree(g.ptr);
+    if (c->gauge_df.ptr) cudaFree(c->gauge_df.ptr);
     for (auto &t : c->nbr)
         if (t) cudaFree(t);
     if (c->partials) cudaFree(c->partials);
@@ -193,6 +194,7 @@ plq_status plq_finalize(plq_ctx *c) {
 long plq_half_volume(const plq_ctx *c) { return c ? (long)c->lat.Vh : 0; }
 
 size_t plq_field_bytes(const plq_ctx *c, int prec, int nrhs) {
+    if (c && prec == PLQ_DF64 && nrhs >= 1 && nrhs <= PLQ_MAX_RHS) return df_site_bytes() * (size_t)c->lat.Vh * nrhs;
     if (!c || !valid_prec(prec) || nrhs < 1 || nrhs > PLQ_MAX_RHS) return 0;
     return spinor_site_bytes(prec) * (size_t)c->lat.Vh * (size_t)nrhs;
 }
@@ -201,10 +203,11 @@ plq_status plq_gauge_upload(plq_ctx *c, const double *U, int is_device, int link
     PLQ_TRY(check_ctx(c));
     if (!U) return set_error(PLQ_ERR_ARG, "null gauge field");
     if (link_reals != 18 && link_reals != 12) return set_error(PLQ_ERR_ARG, "link_reals must be 18 or 12");
-    if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
+    if (!valid_prec(prec) && prec != PLQ_DF64) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
     if (is_device && !aligned16(U)) return set_error(PLQ_ERR_ARG, "gauge pointer not 16-byte aligned");
     PLQ_TRY(use_device(c));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == PLQ_DF64) return df_gauge_upload(c, U, is_device, link_reals, s);
     const size_t V = 2 * (size_t)c->lat.Vh;
     const size_t canon = V * 72 * sizeof(double);
     const double *src = U;
@@ -260,18 +263,20 @@ plq_status plq_gauge_upload(plq_ctx *c, const double *U, int is_device, int link
 plq_status plq_pack_spinor(plq_ctx *c, void *out, const double *in, int prec, int nrhs, void *stream) {
     PLQ_TRY(check_ctx(c));
     if (!aligned16(out) || !aligned16(in)) return set_error(PLQ_ERR_ARG, "null or misaligned field pointer");
-    if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
+    if (!valid_prec(prec) && prec != PLQ_DF64) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
     if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
     PLQ_TRY(use_device(c));
+    if (prec == PLQ_DF64) return df_pack_spinor(c->lat, out, in, nrhs, static_cast<cudaStream_t>(stream));
     return launch_pack_spinor(c->lat, out, in, prec, nrhs, static_cast<cudaStream_t>(stream));
 }
 
 plq_status plq_unpack_spinor(plq_ctx *c, double *out, const void *in, int prec, int nrhs, void *stream) {
     PLQ_TRY(check_ctx(c));
     if (!aligned16(out) || !aligned16(in)) return set_error(PLQ_ERR_ARG, "null or misaligned field pointer");
-    if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
+    if (!valid_prec(prec) && prec != PLQ_DF64) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
     if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
     PLQ_TRY(use_device(c));
+    if (prec == PLQ_DF64) return df_unpack_spinor(c->lat, out, in, nrhs, static_cast<cudaStream_t>(stream));
     return launch_unpack_spinor(c->lat, out, in, prec, nrhs, static_cast<cudaStream_t>(stream));
 }
 
@@ -281,6 +286,10 @@ plq_status plq_hopping_eo(plq_ctx *c, int out_parity, void *out, const void *in,
     if (out == in) return set_error(PLQ_ERR_ARG, "in and out must not overlap");
     if (out_parity != 0 && out_parity != 1) return set_error(PLQ_ERR_ARG, "out_parity must be 0 or 1");
     if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
+    if (prec == PLQ_DF64) {
+        PLQ_TRY(use_device(c));
+        return df_hop(c, out_parity, out, in, nullptr, 0.0, 0.0, 1.0, nrhs, static_cast<cudaStream_t>(stream));
+    }
     PLQ_TRY(need_gauge(c, prec));
     PLQ_TRY(use_device(c));
     HopArgs a = hop_args(c, prec, out_parity, out, in, nrhs);

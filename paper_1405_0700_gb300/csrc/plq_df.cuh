@@ -1,0 +1,94 @@
+// Float-float ("double-float") arithmetic for the FP64-accuracy residuals of
+// the mixed-precision solvers.
+//
+// On this GPU an FP64 fused multiply-add issues at about 1/60 of the FP32
+// rate, so the FP64 hopping operator is bound by its arithmetic, not by
+// memory.  A float-float value is the unevaluated sum hi + lo of two floats
+// (about 48 significant bits, FP32 exponent range); its arithmetic costs ten
+// to twenty FP32 operations per FP64 one, which still leaves it several
+// times faster than FP64 here while reading the same bytes.
+//
+// Building blocks (error-free transformations, all published):
+//   TwoSum      s + e == a + b exactly              (Knuth, TAOCP vol. 2, 4.2.2)
+//   FastTwoSum  the same when |a| >= |b|            (Dekker, Numer. Math. 18, 1971)
+//   TwoProduct  p + e == a * b exactly, through FMA (Ogita, Rump, Oishi,
+//               SIAM J. Sci. Comput. 26, 2005)
+// The round-to-nearest intrinsics keep the compiler from contracting the
+// additions and products these identities rely on into FMAs.
+#pragma once
+
+#include "plq_fields.cuh"
+
+namespace plq {
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// a + b, renormalised (the error of the high parts and both low parts are
+// folded into the new low part)
+__device__ __forceinline__ df operator+(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    const df t = two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+    return t;
+}
+__device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+
+// a * b (the lo * lo term is below the format's precision)
+__device__ __forceinline__ df operator*(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+
+// Exact split of a double into hi = rn(d) and lo = rn(d - hi).
+__device__ __forceinline__ df df_from_double(double d) {
+    const float hi = __double2float_rn(d);
+    return {hi, __double2float_rn(d - (double)hi)};
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// Accumulator of a sum of products: s collects the high parts through TwoSum,
+// e every rounding error and low-order term (one renormalisation at the end).
+struct dacc {
+    float s, e;
+};
+
+// A = x * y (first term of a sum)
+__device__ __forceinline__ dacc dacc_prod(df x, df y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return {p, e};
+}
+
+// A += x * y
+__device__ __forceinline__ void dacc_fma(dacc &A, df x, df y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    const df t = two_sum(A.s, p);
+    A.s = t.hi;
+    A.e = __fadd_rn(A.e, __fadd_rn(t.lo, e));
+}
+
+__device__ __forceinline__ df dacc_value(dacc A) { return two_sum(A.s, A.e); }
+
+}  // namespace plq

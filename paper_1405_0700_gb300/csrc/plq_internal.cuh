@@ -119,6 +119,7 @@ struct Ctx {
     int *nbr[2] = {nullptr, nullptr};  // neighbour tables per output parity (built on demand)
     int device = 0;
     GaugeCopy gauge[3];
+    GaugeCopy gauge_df;  // PLQ_DF64 links (float-float, 18 reals)
     // reduction scratch
     double *partials = nullptr;         // kPartialSlots * kMaxReduceBlocks
     unsigned *ticket = nullptr;
@@ -201,6 +202,18 @@ void apply_tune(const Ctx *c, int prec, int nrhs, HopArgs &a);
 
 // ---------------------------------------------------------------- layouts
 plq_status launch_pack_spinor(const Lattice &lat, void *out, const double *in, int prec, int nrhs, cudaStream_t s);
+
+// ---------------------------------------------------------------- PLQ_DF64 (plq_df.cu)
+size_t df_site_bytes();
+plq_status df_gauge_upload(struct plq_ctx *c, const double *U, int is_device, int link_reals, cudaStream_t s);
+plq_status df_pack_spinor(const Lattice &L, void *out, const double *in, int nrhs, cudaStream_t s);
+plq_status df_unpack_spinor(const Lattice &L, double *out, const void *in, int nrhs, cudaStream_t s);
+// FP64 half field of N elements <-> PLQ_DF64 half field
+plq_status df_split(long long N, void *out, const void *in, cudaStream_t s);
+plq_status df_join(long long N, void *out, const void *in, cudaStream_t s);
+// out = scale_h (1 + i nu_h gamma5) H in, or with x: out = x + a * that (all PLQ_DF64)
+plq_status df_hop(const struct plq_ctx *c, int out_parity, void *out, const void *in, const void *x, double a,
+                  double nu_h, double scale_h, int nrhs, cudaStream_t s);
 plq_status launch_unpack_spinor(const Lattice &lat, double *out, const void *in, int prec, int nrhs, cudaStream_t s);
 plq_status launch_pack_gauge(const Lattice &lat, void *out, const double *in, int prec, int reals, size_t block,
                              unsigned *bad, cudaStream_t s);

@@ -48,6 +48,7 @@ struct Params {
     int use_x0;
     int k;
     double mu;
+    int residual;  // PLQ_F64 or PLQ_DF64 arithmetic of the reliable-update residuals
 };
 
 plq_status parse(const plq_solver_params *p, Params *o) {
@@ -66,6 +67,9 @@ plq_status parse(const plq_solver_params *p, Params *o) {
     if (!valid_prec(o->inner)) return set_error(PLQ_ERR_ARG, "bad inner precision %d", o->inner);
     if (o->delta >= 1.0) return set_error(PLQ_ERR_ARG, "delta must be < 1");
     if (o->k > 256) o->k = 256;
+    o->residual = p ? p->residual_prec : PLQ_F64;
+    if (o->residual != PLQ_F64 && o->residual != PLQ_DF64)
+        return set_error(PLQ_ERR_ARG, "residual_prec must be PLQ_F64 or PLQ_DF64");
     return PLQ_OK;
 }
 
@@ -77,6 +81,24 @@ plq_status true_residual(Solve &S, void *s64, void *tmp_o64, const void *bhat, c
     PLQ_TRY(blas_xpay64(S.N, bhat, -1.0, s64, S.s));  // s = bhat - A x_e
     PLQ_TRY(hop(S, PLQ_F64, 0, s64, tmp_o64, EPI_XPAY_NORM, 0, s64, S.kappa * S.kappa));
     return read_sums(S, s2, S.n);
+}
+
+// The same residual with both half-applications in float-float arithmetic
+// (PLQ_DF64): x_e and bhat - A x_e are split into float-float fields (dfe,
+// even), the odd intermediate lives in dfo; s is joined back into FP64 for
+// the norm and the restart.  A x_e and bhat - A x_e stay FP64.
+plq_status true_residual_df(Solve &S, void *s64, void *dfo, void *dfe, const void *bhat, const void *xe, double *s2) {
+    const Tw t1 = tw_first(S, false);
+    PLQ_TRY(df_split(S.N, dfe, xe, S.s));
+    PLQ_TRY(df_hop(S.c, 1, dfo, dfe, nullptr, 0.0, t1.nu_h, t1.scale_h, S.n, S.s));
+    if (S.nu != 0.0) PLQ_TRY(blas_twist(S.N, s64, xe, PLQ_F64, S.nu, 1.0, S.s));
+    else PLQ_TRY(blas_copy_convert(S.N, s64, PLQ_F64, xe, PLQ_F64, S.s));
+    PLQ_TRY(blas_xpay64(S.N, bhat, -1.0, s64, S.s));
+    PLQ_TRY(df_split(S.N, dfe, s64, S.s));
+    PLQ_TRY(df_hop(S.c, 0, dfe, dfo, dfe, S.kappa * S.kappa, 0.0, 1.0, S.n, S.s));
+    PLQ_TRY(df_join(S.N, s64, dfe, S.s));
+    S.hops += 2;
+    return norm2_64(S, s64, s2);
 }
 
 // zero right-hand side r of an FP64 half field of N elements (n interleaved)
@@ -101,6 +123,9 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
     PLQ_TRY(parse(pp, &P));
     if (!c->gauge[PLQ_F64].ptr) return set_error(PLQ_ERR_STATE, "solvers need the FP64 gauge copy");
     if (!c->gauge[P.inner].ptr) return set_error(PLQ_ERR_STATE, "no gauge copy for inner precision %d", P.inner);
+    const bool df_res = P.residual == PLQ_DF64 && P.inner != PLQ_F64;
+    if (df_res && !c->gauge_df.ptr)
+        return set_error(PLQ_ERR_STATE, "residual_prec = PLQ_DF64 needs the PLQ_DF64 gauge copy");
     PLQ_CUDA(cudaSetDevice(c->device));
 
     Solve S;
@@ -187,7 +212,10 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
 
         const double delta = S.P == PLQ_F64 ? 0.0 : P.delta;
         for (;;) {
-            if ((st = true_residual(S, s64, tmp_o64, bhat, xe, s2.data())) != PLQ_OK) break;
+            // (t64 is free until the final check; it holds the float-float fields)
+            st = df_res ? true_residual_df(S, s64, tmp_o64, t64, bhat, xe, s2.data())
+                        : true_residual(S, s64, tmp_o64, bhat, xe, s2.data());
+            if (st != PLQ_OK) break;
             bool all_done = true;
             for (int r = 0; r < n; ++r) {
                 if (done[r]) continue;

@@ -26,11 +26,11 @@ PLQ_ERR_NAN = 6
 PLQ_ERR_TIMEOUT = 7
 PLQ_ERR_STATE = 8
 
-F64, F32, F16 = 0, 1, 2
+F64, F32, F16, DF64 = 0, 1, 2, 3
 MAX_RHS = 12
 NOALLOC_SCRATCH_BYTES = 8 << 20
-SITE_BYTES = {F64: 192, F32: 96, F16: 52}
-PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16}
+SITE_BYTES = {F64: 192, F32: 96, F16: 52, DF64: 192}
+PREC_NAMES = {"f64": F64, "f32": F32, "f16": F16, "df64": DF64}
 
 # Every function declared in include/plq.h, with (restype, argtypes).
 _c_int, _c_double, _vp, _c_long, _c_size = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_long, ctypes.c_size_t
@@ -45,6 +45,7 @@ class SolverParams(ctypes.Structure):
         ("use_x0", ctypes.c_int),
         ("check_every", ctypes.c_int),
         ("mu", ctypes.c_double),
+        ("residual_prec", ctypes.c_int),
     ]
 
 
@@ -338,8 +339,8 @@ class Context:
 
     # ------------------------------------------------------------ solvers
     def _solve(self, fn, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every, stream, raise_on_error,
-               mu=0.0):
-        p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every, mu)
+               mu=0.0, residual_prec=F64):
+        p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every, mu, prec_of(residual_prec))
         info = SolveInfo()
         st = fn(self._h, _ptr(x), _ptr(b), float(kappa), ctypes.byref(p), ctypes.byref(info), _stream(stream))
         if raise_on_error:
@@ -347,14 +348,16 @@ class Context:
         return info
 
     def cg_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0, use_x0=False,
-                 check_every=16, stream=None, raise_on_error=True, mu=0.0):
-        """CG on the even-odd normal equations; x, b packed full FP64 fields (mu: twisted mass)."""
+                 check_every=16, stream=None, raise_on_error=True, mu=0.0, residual_prec=F64):
+        """CG on the even-odd normal equations; x, b packed full FP64 fields (mu: twisted mass;
+        residual_prec: FP64 or DF64 arithmetic of the reliable-update residuals)."""
         return self._solve(lib().plq_cg_solve, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every,
-                           stream, raise_on_error, mu)
+                           stream, raise_on_error, mu, residual_prec)
 
     def _solve_multi(self, fn, x, b, kappa, nrhs, tol, maxit, inner_prec, delta, use_x0, check_every, stream,
-                     raise_on_error):
-        p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every, 0.0)
+                     raise_on_error, residual_prec=F64):
+        p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), check_every, 0.0,
+                         prec_of(residual_prec))
         infos = (SolveInfo * nrhs)()
         st = fn(self._h, _ptr(x), _ptr(b), float(kappa), nrhs, ctypes.byref(p), infos, _stream(stream))
         if raise_on_error:
@@ -362,21 +365,21 @@ class Context:
         return list(infos)
 
     def cg_solve_multi(self, x, b, kappa, nrhs, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0, use_x0=False,
-                       check_every=16, stream=None, raise_on_error=True):
+                       check_every=16, stream=None, raise_on_error=True, residual_prec=F64):
         """CG for nrhs interleaved right-hand sides (links loaded once per operator application)."""
         return self._solve_multi(lib().plq_cg_solve_multi, x, b, kappa, nrhs, tol, maxit, inner_prec, delta, use_x0,
-                                 check_every, stream, raise_on_error)
+                                 check_every, stream, raise_on_error, residual_prec)
 
     def bicgstab_solve_multi(self, x, b, kappa, nrhs, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0,
-                             use_x0=False, check_every=16, stream=None, raise_on_error=True):
+                             use_x0=False, check_every=16, stream=None, raise_on_error=True, residual_prec=F64):
         return self._solve_multi(lib().plq_bicgstab_solve_multi, x, b, kappa, nrhs, tol, maxit, inner_prec, delta,
-                                 use_x0, check_every, stream, raise_on_error)
+                                 use_x0, check_every, stream, raise_on_error, residual_prec)
 
     def bicgstab_solve(self, x, b, kappa, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0, use_x0=False,
-                       check_every=16, stream=None, raise_on_error=True, mu=0.0):
+                       check_every=16, stream=None, raise_on_error=True, mu=0.0, residual_prec=F64):
         """BiCGstab on the even-odd Schur system; x, b packed full FP64 fields (mu: twisted mass)."""
         return self._solve(lib().plq_bicgstab_solve, x, b, kappa, tol, maxit, inner_prec, delta, use_x0,
-                           check_every, stream, raise_on_error, mu)
+                           check_every, stream, raise_on_error, mu, residual_prec)
 
 
 def cg_solve_batched(ctxs, xs, bs, kappas, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0, use_x0=False,
@@ -387,7 +390,7 @@ def cg_solve_batched(ctxs, xs, bs, kappas, tol=1e-10, maxit=20000, inner_prec=F6
     X = (_vp * n)(*[_ptr(x) for x in xs])
     B = (_vp * n)(*[_ptr(b) for b in bs])
     K = (ctypes.c_double * n)(*[float(k) for k in kappas])
-    p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), 16, 0.0)
+    p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), 16, 0.0, F64)
     infos = (SolveInfo * n)()
     bi = BatchInfo()
     st = lib().plq_cg_solve_batched(H, n, X, B, K, ctypes.byref(p), infos, ctypes.byref(bi), _stream(stream))
@@ -410,7 +413,7 @@ class EigCG:
         return int(lib().plq_eigcg_vectors(self._h))
 
     def solve(self, x, b, kappa, tol=1e-8, maxit=20000, accumulate=True, stream=None, raise_on_error=True):
-        p = SolverParams(tol, maxit, F64, 0.0, 0, 16, 0.0)
+        p = SolverParams(tol, maxit, F64, 0.0, 0, 16, 0.0, F64)
         info = SolveInfo()
         st = lib().plq_eigcg_solve(self._h, _ptr(x), _ptr(b), float(kappa), ctypes.byref(p), int(bool(accumulate)),
                                    ctypes.byref(info), _stream(stream))

@@ -1,7 +1,7 @@
 """Helpers for the GPU parity tests: run the library through its C ABI."""
 import numpy as np
 
-TOL = {0: 1e-13, 1: 2e-6, 2: 5e-3}  # relative L2 per operator application: FP64, FP32, FP16 storage
+TOL = {0: 1e-13, 1: 2e-6, 2: 5e-3, 3: 1e-13}  # relative L2 per operator application: FP64, FP32, FP16, DF64
 
 
 def rel(a, b):

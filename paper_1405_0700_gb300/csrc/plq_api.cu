@@ -172,6 +172,8 @@ plq_status plq_finalize(plq_ctx *c) {
     for (auto &g : c->gauge)
         if (g.ptr) cudaFree(g.ptr);
     if (c->gauge_df.ptr) cudaFree(c->gauge_df.ptr);
+    for (auto &g : c->solve_graph)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto &t : c->nbr)
         if (t) cudaFree(t);
     if (c->partials) cudaFree(c->partials);

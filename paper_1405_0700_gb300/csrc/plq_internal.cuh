@@ -136,6 +136,15 @@ struct Ctx {
     cudaStream_t copy_in = nullptr, copy_out = nullptr, compute = nullptr;  // host-path pipeline
     cudaEvent_t ev[3 * 64] = {};
     int num_sms = 0;
+    // Instantiated inner-iteration graph of the last CG / BiCGstab solve, reused
+    // by the next reliable-update cycle and the next solve with the same key
+    // (method, precisions, sizes, kappa, mu, batch length, workspace address,
+    // launch configuration version).
+    struct SolveGraph {
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long key[10] = {};
+    } solve_graph[2];
+    unsigned tune_version = 0;  // bumped whenever a launch configuration changes
 };
 
 plq_status ensure_work(Ctx *c, size_t bytes);

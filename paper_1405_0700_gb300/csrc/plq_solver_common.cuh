@@ -114,25 +114,38 @@ plq_status get_states(Solve &S, std::vector<SolverState> &st) {
 }
 
 // Run `body` (one inner iteration) as graph-captured batches of `k` until the
-// device state of every right-hand side says stop.
+// device state of every right-hand side says stop.  With a cache, the
+// instantiated graph is kept and reused while the key matches (the body's
+// launches depend only on what the key records).
 template <class Body>
-plq_status run_batches(Solve &S, int k, Body body, std::vector<SolverState> &cur) {
-    cudaGraph_t graph = nullptr;
+plq_status run_batches(Solve &S, int k, Body body, std::vector<SolverState> &cur, Ctx::SolveGraph *cache = nullptr,
+                       const unsigned long long *key = nullptr) {
     cudaGraphExec_t exec = nullptr;
-    PLQ_CUDA(cudaStreamBeginCapture(S.s, cudaStreamCaptureModeThreadLocal));
     plq_status st = PLQ_OK;
-    const double hops0 = S.hops;
-    for (int i = 0; i < k && st == PLQ_OK; ++i) st = body();
-    cudaError_t e = cudaStreamEndCapture(S.s, &graph);
-    S.hops = hops0;
-    if (st != PLQ_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return st;
+    cudaError_t e = cudaSuccess;
+    if (cache && cache->exec && std::memcmp(cache->key, key, sizeof(cache->key)) == 0) {
+        exec = cache->exec;
+    } else {
+        cudaGraph_t graph = nullptr;
+        PLQ_CUDA(cudaStreamBeginCapture(S.s, cudaStreamCaptureModeThreadLocal));
+        const double hops0 = S.hops;
+        for (int i = 0; i < k && st == PLQ_OK; ++i) st = body();
+        e = cudaStreamEndCapture(S.s, &graph);
+        S.hops = hops0;
+        if (st != PLQ_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+        if (cache) {
+            if (cache->exec) cudaGraphExecDestroy(cache->exec);
+            cache->exec = exec;
+            std::memcpy(cache->key, key, sizeof(cache->key));
+        }
     }
-    if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
     long long last_sum = -1;
     int idle = 0;
     for (;;) {
@@ -159,7 +172,7 @@ plq_status run_batches(Solve &S, int k, Body body, std::vector<SolverState> &cur
             break;
         }
     }
-    cudaGraphExecDestroy(exec);
+    if (!cache) cudaGraphExecDestroy(exec);
     return st;
 }
 

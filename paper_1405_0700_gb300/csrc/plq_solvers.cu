@@ -149,6 +149,20 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
     void *L[7];
     for (int i = 0; i < nL; ++i) L[i] = wl + i * hL;
     void *xL = wl + nL * hL;
+    // key of the inner-iteration graph (see Ctx::SolveGraph)
+    unsigned long long gkey[10] = {};
+    {
+        double kk = kappa, nu = S.nu;
+        gkey[0] = (unsigned long long)method;
+        gkey[1] = (unsigned long long)S.P | ((unsigned long long)S.PX << 8) | ((unsigned long long)n << 16);
+        gkey[2] = (unsigned long long)S.N;
+        std::memcpy(&gkey[3], &kk, sizeof(double));
+        std::memcpy(&gkey[4], &nu, sizeof(double));
+        gkey[5] = (unsigned long long)P.k;
+        gkey[6] = (unsigned long long)reinterpret_cast<uintptr_t>(c->work);
+        gkey[7] = (unsigned long long)c->tune_version;
+        gkey[8] = 1;  // marks a valid key
+    }
 
     // internal stream ordered after the caller's stream
     cudaStream_t user = static_cast<cudaStream_t>(stream);
@@ -308,7 +322,7 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
                     PLQ_TRY(blas_cg_update(S.N, n, xL, rL, pL, qL, PI, rb, c->state, s));
                     return blas_cg_direction(S.N, n, pL, rL, PI, c->state, s);
                 };
-                if ((st = run_batches(S, P.k, body, fin)) != PLQ_OK) break;
+                if ((st = run_batches(S, P.k, body, fin, &c->solve_graph[method], gkey)) != PLQ_OK) break;
             } else {
                 void *rL = L[0], *rhL = L[1], *pL = L[2], *vL = L[3], *sL = L[4], *tL = L[5], *toL = L[6];
                 if ((st = blas_copy_convert(S.N, rL, S.P, s64, PLQ_F64, s)) != PLQ_OK) break;
@@ -337,7 +351,7 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
                     PLQ_TRY(blas_bicg_update(S.N, n, xL, rL, pL, sL, tL, rhL, PI, rb, c->state, s));
                     return blas_bicg_p(S.N, n, pL, rL, vL, PI, c->state, s);
                 };
-                if ((st = run_batches(S, P.k, body, fin)) != PLQ_OK) break;
+                if ((st = run_batches(S, P.k, body, fin, &c->solve_graph[method], gkey)) != PLQ_OK) break;
             }
             for (int r = 0; r < n; ++r) {
                 if (done[r]) continue;

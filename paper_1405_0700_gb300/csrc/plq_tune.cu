@@ -114,6 +114,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
     if (path && cache_lookup(path, key, &best)) {
         if (best.index_mode == 1) PLQ_TRY(ensure_nbr_tables(c));
         c->tune[prec][nrhs] = best;
+        ++c->tune_version;
         if (res) {
             res->block = best.block;
             res->index_mode = best.index_mode;
@@ -211,6 +212,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
     cudaFree(out);
     if (st != PLQ_OK) return st;
     c->tune[prec][nrhs] = best;
+    ++c->tune_version;
     if (path) cache_store(path, key, best);
     if (res) {
         res->block = best.block;
@@ -244,5 +246,6 @@ extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, 
     c->tune[prec][nrhs].rhs_tile = rhs_tile;
     c->tune[prec][nrhs].zc = z_chunk;
     c->tune[prec][nrhs].smem_links = smem_links ? 1 : 0;
+    ++c->tune_version;
     return PLQ_OK;
 }

@@ -125,8 +125,9 @@ typedef struct {
     int check_every;   /* inner iterations per host convergence poll, default 16           */
     double mu;         /* twisted mass: solve M_tm = 1 - kappa H + 2 i kappa mu gamma5
                           (0: the Wilson operator M)                                        */
-    int residual_prec; /* arithmetic of the reliable-update residuals s = bhat - Mhat x of a
-                          mixed-precision solve: PLQ_F64 (default) or PLQ_DF64 (needs the
+    int residual_prec; /* arithmetic of the FP64-accuracy steps of a mixed-precision solve
+                          (bhat, the reliable-update residuals s = bhat - Mhat x and the
+                          odd solution x_o): PLQ_F64 (default) or PLQ_DF64 (needs the
                           PLQ_DF64 gauge copy).  The residual of the returned x is always
                           computed in FP64.  Used by plq_cg_solve(_multi) and
                           plq_bicgstab_solve(_multi); other solvers ignore it.               */

@@ -218,11 +218,19 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
         }
         // bhat = b_e + kappa H_eo A^{-1} b_o (A = 1 for Wilson)
         const void *bsrc = bo;
-        if (S.nu != 0.0) {
-            if ((st = blas_twist(S.N, tmp_o64, bo, PLQ_F64, -S.nu, 1.0 / (1.0 + S.nu * S.nu), s)) != PLQ_OK) break;
-            bsrc = tmp_o64;
+        if (S.nu != 0.0) {  // (r64 is free until the iteration starts)
+            if ((st = blas_twist(S.N, r64, bo, PLQ_F64, -S.nu, 1.0 / (1.0 + S.nu * S.nu), s)) != PLQ_OK) break;
+            bsrc = r64;
         }
-        if ((st = hop(S, PLQ_F64, 0, bhat, bsrc, EPI_XPAY, 0, be, kappa)) != PLQ_OK) break;
+        if (df_res) {  // in float-float: t64 / tmp_o64 hold the split fields
+            if ((st = df_split(S.N, tmp_o64, bsrc, s)) != PLQ_OK) break;
+            if ((st = df_split(S.N, t64, be, s)) != PLQ_OK) break;
+            if ((st = df_hop(c, 0, t64, tmp_o64, t64, kappa, 0.0, 1.0, n, s)) != PLQ_OK) break;
+            if ((st = df_join(S.N, bhat, t64, s)) != PLQ_OK) break;
+            S.hops += 1;
+        } else if ((st = hop(S, PLQ_F64, 0, bhat, bsrc, EPI_XPAY, 0, be, kappa)) != PLQ_OK) {
+            break;
+        }
 
         const double delta = S.P == PLQ_F64 ? 0.0 : P.delta;
         for (;;) {
@@ -380,7 +388,15 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
         }
         if (st != PLQ_OK) break;
         // x_o = A^{-1} (b_o + kappa H_oe x_e)
-        if ((st = hop(S, PLQ_F64, 1, xo, xe, EPI_XPAY, 0, bo, kappa)) != PLQ_OK) break;
+        if (df_res) {
+            if ((st = df_split(S.N, t64, xe, s)) != PLQ_OK) break;
+            if ((st = df_split(S.N, tmp_o64, bo, s)) != PLQ_OK) break;
+            if ((st = df_hop(c, 1, tmp_o64, t64, tmp_o64, kappa, 0.0, 1.0, n, s)) != PLQ_OK) break;
+            if ((st = df_join(S.N, xo, tmp_o64, s)) != PLQ_OK) break;
+            S.hops += 1;
+        } else if ((st = hop(S, PLQ_F64, 1, xo, xe, EPI_XPAY, 0, bo, kappa)) != PLQ_OK) {
+            break;
+        }
         if (S.nu != 0.0 && (st = blas_twist(S.N, xo, xo, PLQ_F64, -S.nu, 1.0 / (1.0 + S.nu * S.nu), s)) != PLQ_OK)
             break;
         // full true residual ||b - M x|| with the FP64 operator, both parities

@@ -242,6 +242,82 @@ def roofline_entry(ms, vh, prec_name, reals, peak_gbs):
             "gbs_no_reuse_convention": NO_REUSE[(prec_name, reals)] * vh / (ms * 1e-3) / 1e9}
 
 
+def theta_section(ctx, torch, U, phi, vh, peak, variants):
+    """Eq. (2) taken literally: the two-pass theta-field schedule against the fused
+    gather kernel on the same half-application (FP32 and FP64, 18-real links)."""
+    from paper_1405_0700_gb300 import F32, F64
+
+    out = {}
+    for pname, prec in (("f32", F32), ("f64", F64)):
+        ctx.gauge_upload(U, 18, prec)
+        full = ctx.to_device(phi, prec)
+        _, o_in = ctx.halves(full, prec)
+        o = ctx.empty_half(prec)
+        th = torch.empty(ctx.theta_bytes(prec), dtype=torch.uint8, device=o.device)
+        reps = 20 if prec == F32 else 5
+        for _ in range(3):
+            ctx.hopping_eo_theta(0, o, o_in, th, prec)
+        torch.cuda.synchronize()
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record()
+        for _ in range(reps):
+            ctx.hopping_eo_theta(0, o, o_in, th, prec)
+        e_.record()
+        torch.cuda.synchronize()
+        ms = s_.elapsed_time(e_) / reps
+        # pass 1: input spinor + 4 backward links in, 8 theta half spinors out;
+        # pass 2: 8 theta half spinors + 4 forward links in, output spinor out
+        sp, lk, half = (96, 72, 48) if prec == F32 else (192, 144, 96)
+        per_site = 2 * sp + 8 * lk + 16 * half
+        fused = variants[f"{pname}_18"]["ms"]
+        out[pname] = {"ms": ms, "fused_ms": fused, "slowdown_vs_fused": ms / fused,
+                      "bytes_per_site": per_site, "gbs": per_site * vh / (ms * 1e-3) / 1e9,
+                      "frac_of_measured_hbm": per_site * vh / (ms * 1e-3) / 1e9 / peak}
+        log(f"[bench] theta two-pass {pname}: {ms * 1e3:.1f} us (fused {fused * 1e3:.1f} us)")
+        del full, o, th
+    return out
+
+
+def stream_section(torch, quick):
+    """The link x spinor streaming kernel (psi(i) = U(i) phi(i), site records as in
+    the paper's CPU code) with sequential, index-array and pointer-array access, on
+    a working set inside L2 (2^16 sites, 17 MB) and far outside it (2^24, 4.4 GB)."""
+    from paper_1405_0700_gb300 import F32
+    from paper_1405_0700_gb300 import plq as P
+
+    out = {}
+    for n in ((1 << 16), (1 << 24) if not quick else (1 << 20)):
+        g = torch.Generator(device="cuda").manual_seed(11)
+        U = torch.randn(n * 18, device="cuda", generator=g)
+        ph = torch.randn(n * 24, device="cuda", generator=g)
+        psi = torch.empty_like(ph)
+        perm = torch.randperm(n, device="cuda", generator=g).to(torch.int32)
+        es = ph.element_size()
+        pl = perm.long()
+        ptrs = torch.cat([psi.data_ptr() + pl * (24 * es), U.data_ptr() + pl * (18 * es),
+                          ph.data_ptr() + pl * (24 * es)]).contiguous()
+        res = {}
+        for mode, name in ((0, "sequential"), (1, "index_array"), (2, "pointer_array")):
+            args = (mode, n, U, ph, psi, perm if mode == 1 else None, ptrs if mode == 2 else None, F32)
+            for _ in range(3):
+                P.link_spinor_stream(*args)
+            torch.cuda.synchronize()
+            reps = 200 if n <= (1 << 16) else 10
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record()
+            for _ in range(reps):
+                P.link_spinor_stream(*args)
+            e_.record()
+            torch.cuda.synchronize()
+            ms = s_.elapsed_time(e_) / reps
+            nbytes = n * (72 + 96 + 96) + (4 * n if mode == 1 else 24 * n if mode == 2 else 0)
+            res[name] = {"ms": ms, "gbs": nbytes / (ms * 1e-3) / 1e9}
+        out[f"{n}_sites"] = res
+        log(f"[bench] stream n={n}: " + ", ".join(f"{k} {v['gbs']:.0f} GB/s" for k, v in res.items()))
+        del U, ph, psi, perm, ptrs, pl
+    return out
+
+
 def cg_section(torch, local_rank, quick):
     from paper_1405_0700_gb300 import DF64, F16, F32, F64, Context
 
@@ -553,7 +629,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small lattices (smoke use only)")
     ap.add_argument("--source-hash", action="store_true", help="print the hash of the headline kernel's sources")
-    ap.add_argument("--workload", default="hop", choices=["hop", "propagator", "operator", "eigcg", "batch"],
+    ap.add_argument("--workload", default="hop", choices=["hop", "propagator", "operator", "eigcg", "batch", "stream"],
                     help="hop: the headline operator line (default); propagator: 48^3x96 with 12 point sources")
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "df64"])
     ap.add_argument("--links", type=int, default=18, choices=[18, 12])
@@ -581,6 +657,9 @@ def main():
 
     torch.cuda.set_device(local_rank)
     lib()
+    if args.workload == "stream":
+        print(json.dumps({"workload": "stream", **stream_section(torch, args.quick)}), flush=True)
+        return
     if args.workload == "operator":
         # one operator configuration alone (used for profiling): --lattice, --prec, --links, --nrhs
         return operator_only(args, torch, local_rank)
@@ -673,7 +752,9 @@ def main():
         variants[f"{pname}_{reals}"] = dict(roofline_entry(msv, vh, pname, reals, peak), launch=tuned_v)
         del fv, outv
         log(f"[bench] {pname}-{reals}: {msv * 1e3:.1f} us, {variants[f'{pname}_{reals}']['gbs_compulsory']:.0f} GB/s")
+    theta = theta_section(ctx, torch, U, phi, vh, peak, variants)
     ctx.close()
+    stream = stream_section(torch, args.quick)
 
     cg = None
     if not args.no_cg:
@@ -716,6 +797,8 @@ def main():
             "gbs_no_reuse_convention": head["gbs_no_reuse_convention"],
             "variants": variants,
             "cg": cg,
+            "theta_two_pass": theta,
+            "link_spinor_stream": stream,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),

@@ -403,7 +403,6 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(const HopArgs a) {
 #pragma unroll
             for (int e = 0; e < 9; ++e) sU[k][d][e] = u[e / 3][e % 3];
             sJ[k][d] = j | (flip ? (int)0x80000000u : 0);
-            if (d == 0) sJ[k][0] |= 0;  // (index of the site itself is not needed)
         }
         __syncthreads();
         const int k = threadIdx.y;

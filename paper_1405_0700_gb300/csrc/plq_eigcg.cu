@@ -20,6 +20,14 @@
 // small dense eigenproblem on the host (Jacobi, at most m = 64) and one
 // linear-combination kernel over V on the device; Gram-Schmidt and the
 // projections onto U are multi-vector dot / axpy kernels.
+//
+// Precision.  The CG iterations, H = U^H A U, the Galerkin start and every
+// residual are FP64.  The search space V (Lanczos vectors, restarts, Ritz
+// vectors) and the Gram-Schmidt orthogonalisation of new basis vectors work
+// on FP32 copies: they only shape the deflation subspace, whose Galerkin
+// projection is exact for whatever vectors U holds (H is computed for those
+// vectors), while in FP64 these dense multi-vector sweeps are bound by this
+// GPU's FP64 FMA rate (~1/60 of FP32) and dominate the accumulation phase.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -33,9 +41,11 @@ struct plq_eigcg {
     plq_ctx *ctx = nullptr;
     int nev = 10, m = 60, max_vectors = 300;
     int nvec = 0;                        // vectors in U
-    double2 *U = nullptr;                // max_vectors slots
-    double2 *V = nullptr, *V2 = nullptr; // m + 1 slots each (double buffer for restarts)
-    double2 *work = nullptr;             // 4 slots: Aw, tmp, ...
+    double2 *U = nullptr;                // max_vectors slots (FP64)
+    float2 *U32 = nullptr;               // the same vectors in FP32 (Gram-Schmidt)
+    float2 *V = nullptr, *V2 = nullptr;  // m + 1 FP32 slots each (double buffer for restarts)
+    double2 *work = nullptr;             // 4 slots: Aw, w, odd and even temporaries
+    float2 *work32 = nullptr;            // 1 slot: w in FP32
     double *hist = nullptr;              // device history of CG coefficients
     int hist_cap = 0;
     double *coef = nullptr;              // device coefficient matrix (lincomb)
@@ -159,28 +169,82 @@ int grid_of(long long work, bool reduce) {
     return (int)(want < cap ? want : cap);
 }
 
-// out_l = sum_i C[i*k + l] * in_i  for l < k (real coefficients; slots `stride` apart)
-__global__ void lincomb_kernel(long long N, const double2 *in, size_t stride, int m, const double *C, int k,
-                               double2 *out, size_t out_stride) {
-    __shared__ double Cs[kMaxM * 24];
+// out_l = sum_i C[i*k + l] * in_i  for l < k (real coefficients; FP32 slots `stride` apart)
+__global__ void lincomb32_kernel(long long N, const float2 *in, size_t stride, int m, const float *C, int k,
+                                 float2 *out, size_t out_stride) {
+    __shared__ float Cs[kMaxM * 24];
     for (int t = threadIdx.x; t < m * k; t += blockDim.x) Cs[t] = C[t];
     __syncthreads();
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
-        double2 acc[24];
+        float2 acc[24];
 #pragma unroll
-        for (int l = 0; l < 24; ++l) acc[l] = make_double2(0.0, 0.0);
+        for (int l = 0; l < 24; ++l) acc[l] = make_float2(0.f, 0.f);
         for (int i = 0; i < m; ++i) {
-            const double2 v = __ldg(in + i * stride + e);
+            const float2 v = __ldg(in + i * stride + e);
 #pragma unroll
             for (int l = 0; l < 24; ++l)
                 if (l < k) {
-                    acc[l].x = fma(Cs[i * k + l], v.x, acc[l].x);
-                    acc[l].y = fma(Cs[i * k + l], v.y, acc[l].y);
+                    acc[l].x = fmaf(Cs[i * k + l], v.x, acc[l].x);
+                    acc[l].y = fmaf(Cs[i * k + l], v.y, acc[l].y);
                 }
         }
 #pragma unroll
         for (int l = 0; l < 24; ++l)
             if (l < k) out[l * out_stride + e] = acc[l];
+    }
+}
+
+__global__ void to32_kernel(long long N, float2 *out, const double2 *in) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const double2 a = in[e];
+        out[e] = make_float2((float)a.x, (float)a.y);
+    }
+}
+
+__global__ void to64_kernel(long long N, double2 *out, const float2 *in) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const float2 a = in[e];
+        out[e] = make_double2((double)a.x, (double)a.y);
+    }
+}
+
+// out = base + sum_i c_i in_i over FP32 slots (complex coefficients; base may alias out)
+__global__ void zlincomb32_kernel(long long N, const float2 *in, size_t stride, int m, const double2 *c,
+                                  const float2 *base, float2 *out) {
+    __shared__ float2 cs[kDotChunk];
+    for (int t = threadIdx.x; t < m; t += blockDim.x) cs[t] = make_float2((float)c[t].x, (float)c[t].y);
+    __syncthreads();
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        float2 a = base ? base[e] : make_float2(0.f, 0.f);
+        for (int i = 0; i < m; ++i) {
+            const float2 v = __ldg(in + i * stride + e), w = cs[i];
+            a.x = fmaf(w.x, v.x, fmaf(-w.y, v.y, a.x));
+            a.y = fmaf(w.x, v.y, fmaf(w.y, v.x, a.y));
+        }
+        out[e] = a;
+    }
+}
+
+// d_i = <u_i, w> for i < cnt (<= kDotChunk), FP32 slots; per-thread FP32 partial
+// sums (a handful of elements each), FP64 across threads and blocks
+__global__ void multidot32_kernel(long long N, const float2 *U, size_t stride, int cnt, const float2 *w, Reduce red) {
+    RedAcc<2 * kDotChunk, float> acc;
+    red_init(acc, 1);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const float2 b = w[e];
+        for (int i = 0; i < cnt; ++i) {
+            const float2 a = __ldg(U + i * stride + e);
+            acc.v[2 * i] += a.x * b.x + a.y * b.y;
+            acc.v[2 * i + 1] += a.x * b.y - a.y * b.x;
+        }
+    }
+    grid_reduce(red, acc);
+}
+
+__global__ void scale32_kernel(long long N, float2 *v, float s) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const float2 a = v[e];
+        v[e] = make_float2(s * a.x, s * a.y);
     }
 }
 
@@ -214,13 +278,6 @@ __global__ void multidot_kernel(long long N, const double2 *U, size_t stride, in
         }
     }
     grid_reduce(red, acc);
-}
-
-__global__ void scale_kernel(long long N, double2 *v, double s) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
-        const double2 a = v[e];
-        v[e] = make_double2(s * a.x, s * a.y);
-    }
 }
 
 struct Eig {
@@ -264,10 +321,42 @@ plq_status zcomb(Eig &G, const double2 *Ubase, const std::vector<std::complex<do
     return PLQ_OK;
 }
 
-// out_l = sum_i C[i*k + l] in_i (real, k <= 24, m <= kMaxM)
-plq_status rcomb(Eig &G, const double2 *in, int m, const std::vector<double> &C, int k, double2 *out) {
-    PLQ_CUDA(cudaMemcpyAsync(G.E->coef, C.data(), sizeof(double) * m * k, cudaMemcpyHostToDevice, G.S.s));
-    lincomb_kernel<<<grid_of(G.N, false), 256, 0, G.S.s>>>(G.N, in, G.E->slot, m, G.E->coef, k, out, G.E->slot);
+plq_status dots32(Eig &G, const float2 *Ubase, int cnt, const float2 *w, std::vector<std::complex<double>> &d) {
+    d.assign(cnt, {0, 0});
+    for (int c0 = 0; c0 < cnt; c0 += kDotChunk) {
+        const int c = std::min(kDotChunk, cnt - c0);
+        Reduce r = reduce_of(G.S.c, FIN_NONE);
+        r.st = nullptr;
+        multidot32_kernel<<<grid_of(G.N, true), 256, 0, G.S.s>>>(G.N, Ubase + c0 * G.E->slot, G.E->slot, c, w, r);
+        PLQ_CUDA(cudaGetLastError());
+        double buf[2 * kDotChunk];
+        PLQ_TRY(read_sums(G.S, buf, 2 * c));
+        for (int i = 0; i < c; ++i) d[c0 + i] = {buf[2 * i], buf[2 * i + 1]};
+    }
+    return PLQ_OK;
+}
+
+// w += sum_i c_i U32_i, in chunks (FP32)
+plq_status zcomb32(Eig &G, const float2 *Ubase, const std::vector<std::complex<double>> &c, float2 *w) {
+    const int cnt = (int)c.size();
+    double2 *cdev = reinterpret_cast<double2 *>(G.E->coef);
+    for (int c0 = 0; c0 < cnt; c0 += kDotChunk) {
+        const int k = std::min(kDotChunk, cnt - c0);
+        PLQ_CUDA(cudaMemcpyAsync(cdev, c.data() + c0, k * sizeof(double2), cudaMemcpyHostToDevice, G.S.s));
+        zlincomb32_kernel<<<grid_of(G.N, false), 256, 0, G.S.s>>>(G.N, Ubase + c0 * G.E->slot, G.E->slot, k, cdev,
+                                                                  w, w);
+        PLQ_CUDA(cudaGetLastError());
+        PLQ_CUDA(cudaStreamSynchronize(G.S.s));  // cdev is reused by the next chunk
+    }
+    return PLQ_OK;
+}
+
+// out_l = sum_i C[i*k + l] in_i over FP32 slots (real, k <= 24, m <= kMaxM)
+plq_status rcomb(Eig &G, const float2 *in, int m, const std::vector<double> &C, int k, float2 *out) {
+    std::vector<float> Cf(C.begin(), C.begin() + (size_t)m * k);
+    float *cdev = reinterpret_cast<float *>(G.E->coef);
+    PLQ_CUDA(cudaMemcpyAsync(cdev, Cf.data(), sizeof(float) * m * k, cudaMemcpyHostToDevice, G.S.s));
+    lincomb32_kernel<<<grid_of(G.N, false), 256, 0, G.S.s>>>(G.N, in, G.E->slot, m, cdev, k, out, G.E->slot);
     PLQ_CUDA(cudaGetLastError());
     PLQ_CUDA(cudaStreamSynchronize(G.S.s));
     return PLQ_OK;
@@ -282,22 +371,28 @@ plq_status apply_A(Eig &G, double2 *y, const double2 *v, void *tmp_o, void *tmp_
     return hop(G.S, PLQ_F64, 0, y, tmp_o, EPI_XPAY, 1, tmp_e, -kk);
 }
 
-// Add the vectors w (in the slots of `src`, count cnt) to the deflation basis.
-plq_status add_to_basis(Eig &G, const double2 *src, int cnt, void *tmp_o, void *tmp_e) {
+// Add the vectors w (FP32, in the slots of `src`, count cnt) to the deflation
+// basis: classical Gram-Schmidt twice against U in FP32, normalisation, then
+// the new row and column of H = U^H A U in FP64 for the FP64 copy of w.
+plq_status add_to_basis(Eig &G, const float2 *src, int cnt, void *tmp_o, void *tmp_e) {
     plq_eigcg *E = G.E;
     double2 *Aw = E->work, *w = E->work + E->slot;
+    float2 *w32 = E->work32;
     for (int q = 0; q < cnt && E->nvec < E->max_vectors; ++q) {
-        PLQ_CUDA(cudaMemcpyAsync(w, src + q * E->slot, G.N * sizeof(double2), cudaMemcpyDeviceToDevice, G.S.s));
+        PLQ_CUDA(cudaMemcpyAsync(w32, src + q * E->slot, G.N * sizeof(float2), cudaMemcpyDeviceToDevice, G.S.s));
         std::vector<std::complex<double>> d;
-        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-            PLQ_TRY(dots(G, E->U, E->nvec, w, d));
+        for (int pass = 0; pass < 2 && E->nvec > 0; ++pass) {  // classical Gram-Schmidt, twice
+            PLQ_TRY(dots32(G, E->U32, E->nvec, w32, d));
             for (auto &z : d) z = -z;
-            PLQ_TRY(zcomb(G, E->U, d, w, w));
+            PLQ_TRY(zcomb32(G, E->U32, d, w32));
         }
-        double n2 = 0;
-        PLQ_TRY(norm2_64(G.S, w, &n2));
+        std::vector<std::complex<double>> nn;
+        PLQ_TRY(dots32(G, w32, 1, w32, nn));
+        const double n2 = std::real(nn[0]);
         if (!(n2 > 1e-20)) continue;  // linearly dependent: skip
-        scale_kernel<<<grid_of(G.N, false), 256, 0, G.S.s>>>(G.N, w, 1.0 / std::sqrt(n2));
+        scale32_kernel<<<grid_of(G.N, false), 256, 0, G.S.s>>>(G.N, w32, (float)(1.0 / std::sqrt(n2)));
+        PLQ_CUDA(cudaGetLastError());
+        to64_kernel<<<grid_of(G.N, false), 256, 0, G.S.s>>>(G.N, w, w32);
         PLQ_CUDA(cudaGetLastError());
         PLQ_TRY(apply_A(G, Aw, w, tmp_o, tmp_e));
         std::vector<std::complex<double>> col;
@@ -311,6 +406,7 @@ plq_status add_to_basis(Eig &G, const double2 *src, int cnt, void *tmp_o, void *
         }
         E->H[(size_t)k * ld + k] = std::real(self[0]);
         PLQ_CUDA(cudaMemcpyAsync(E->U + k * E->slot, w, G.N * sizeof(double2), cudaMemcpyDeviceToDevice, G.S.s));
+        PLQ_CUDA(cudaMemcpyAsync(E->U32 + k * E->slot, w32, G.N * sizeof(float2), cudaMemcpyDeviceToDevice, G.S.s));
         E->nvec += 1;
     }
     PLQ_CUDA(cudaStreamSynchronize(G.S.s));
@@ -335,12 +431,14 @@ extern "C" plq_status plq_eigcg_create(plq_ctx *ctx, int nev, int m, int max_vec
     E->m = m;
     E->max_vectors = max_vectors;
     E->slot = 12 * (size_t)ctx->lat.Vh;
-    const size_t sb = E->slot * sizeof(double2);
+    const size_t sb = E->slot * sizeof(double2), sb32 = E->slot * sizeof(float2);
     E->hist_cap = 1 << 16;
     cudaError_t e = cudaMalloc(&E->U, sb * max_vectors);
-    if (e == cudaSuccess) e = cudaMalloc(&E->V, sb * (m + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&E->V2, sb * (m + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&E->U32, sb32 * max_vectors);
+    if (e == cudaSuccess) e = cudaMalloc(&E->V, sb32 * (m + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&E->V2, sb32 * (m + 1));
     if (e == cudaSuccess) e = cudaMalloc(&E->work, sb * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&E->work32, sb32);
     if (e == cudaSuccess) e = cudaMalloc(&E->hist, sizeof(double) * 3 * E->hist_cap);
     if (e == cudaSuccess) e = cudaMalloc(&E->coef, sizeof(double) * kMaxM * 24 * 2);
     if (e != cudaSuccess) {
@@ -357,7 +455,8 @@ extern "C" plq_status plq_eigcg_destroy(plq_eigcg *E) {
     if (!E) return PLQ_OK;
     cudaSetDevice(E->ctx->device);
     cudaDeviceSynchronize();
-    for (void *p : {(void *)E->U, (void *)E->V, (void *)E->V2, (void *)E->work, (void *)E->hist, (void *)E->coef})
+    for (void *p : {(void *)E->U, (void *)E->U32, (void *)E->V, (void *)E->V2, (void *)E->work, (void *)E->work32,
+                    (void *)E->hist, (void *)E->coef})
         if (p) cudaFree(p);
     delete E;
     return PLQ_OK;
@@ -441,7 +540,8 @@ extern "C" plq_status plq_eigcg_solve(plq_eigcg *E, void *x, const void *b, doub
         std::vector<double> T((size_t)(m + 1) * (m + 1), 0.0), nrm(m + 1, 1.0);
         int vs = 1;  // V slot 0 holds r_0 (raw)
         if (eig) {
-            PLQ_CUDA(cudaMemcpyAsync(E->V, r, h64, cudaMemcpyDeviceToDevice, s));
+            to32_kernel<<<grid_of(G.N, false), 256, 0, s>>>(G.N, E->V, static_cast<const double2 *>(r));
+            PLQ_CUDA(cudaGetLastError());
             nrm[0] = std::sqrt(rho0);
         }
         double alpha_prev = 0, beta_prev = 0;
@@ -461,7 +561,7 @@ extern "C" plq_status plq_eigcg_solve(plq_eigcg *E, void *x, const void *b, doub
             std::vector<SolverState> sv(1, init);
             if ((st = put_states(G.S, sv)) != PLQ_OK) break;
             const int L = eig ? (m - vs + 1) : 16;
-            double2 *Vb = E->V;
+            float2 *Vb = E->V;
             auto body = [&](int i) -> plq_status {
                 PLQ_TRY(hop(G.S, PLQ_F64, 1, to, p, EPI_PLAIN, 0, nullptr, 0.0, FIN_NONE, nullptr, true));
                 PLQ_TRY(hop(G.S, PLQ_F64, 0, mp, to, EPI_XPAY_NORM, 0, p, -kk, FIN_CG_ALPHA, nullptr, true));
@@ -469,8 +569,11 @@ extern "C" plq_status plq_eigcg_solve(plq_eigcg *E, void *x, const void *b, doub
                 PLQ_TRY(hop(G.S, PLQ_F64, 0, q, to, EPI_XPAY, 1, mp, -kk, FIN_NONE, nullptr, true));
                 Reduce rb = reduce_of(c, FIN_CG_BETA);
                 PLQ_TRY(blas_cg_update(G.S.N, 1, xe, r, p, q, PLQ_F64, rb, c->state, s));
-                if (eig)  // raw r_{j+1} into its slot of the search space
-                    PLQ_CUDA(cudaMemcpyAsync(Vb + (size_t)(vs + i) * E->slot, r, h64, cudaMemcpyDeviceToDevice, s));
+                if (eig) {  // raw r_{j+1} into its (FP32) slot of the search space
+                    to32_kernel<<<grid_of(G.N, false), 256, 0, s>>>(G.N, Vb + (size_t)(vs + i) * E->slot,
+                                                                    static_cast<const double2 *>(r));
+                    PLQ_CUDA(cudaGetLastError());
+                }
                 return blas_cg_direction(G.S.N, 1, p, r, PLQ_F64, c->state, s);
             };
             // one graph of exactly L iterations (the ones that fill V)
@@ -560,8 +663,8 @@ extern "C" plq_status plq_eigcg_solve(plq_eigcg *E, void *x, const void *b, doub
                             C[(size_t)i2 * k2 + l] = sacc / nrm[i2];  // raw slots -> normalised V
                         }
                     if ((st = rcomb(G, E->V, m, C, k2, E->V2)) != PLQ_OK) break;
-                    PLQ_CUDA(cudaMemcpyAsync(E->V2 + (size_t)k2 * E->slot, E->V + (size_t)m * E->slot, h64,
-                                             cudaMemcpyDeviceToDevice, s));
+                    PLQ_CUDA(cudaMemcpyAsync(E->V2 + (size_t)k2 * E->slot, E->V + (size_t)m * E->slot,
+                                             G.N * sizeof(float2), cudaMemcpyDeviceToDevice, s));
                     std::swap(E->V, E->V2);
                     const double tlast = -std::sqrt(beta_prev) / alpha_prev;
                     std::fill(T.begin(), T.end(), 0.0);

@@ -265,7 +265,8 @@ PLQ_API plq_status plq_bicgstab_solve_multi(plq_ctx *ctx, void *x, const void *b
  * Mhat^dag Mhat (even-odd normal equations) and H = U^H A U.
  *   plq_eigcg_create: nev Ritz vectors per accumulating solve, search space m
  *     (2*nev + 2 <= m <= 64, 2*nev <= 24), room for max_vectors basis vectors
- *     (device memory: max_vectors + 2*(m+1) + 4 FP64 half fields).
+ *     (device memory: max_vectors + 4 FP64 half fields and max_vectors +
+ *     2*(m+1) + 1 FP32 ones).
  *   plq_eigcg_solve: solves M x = b (packed full FP64 fields).  The Krylov
  *     solve on the normal equations starts from the Galerkin guess
  *     x0 = U H^{-1} U^H rhs; with accumulate != 0 (and room left in U) it is
@@ -273,7 +274,11 @@ PLQ_API plq_status plq_bicgstab_solve_multi(plq_ctx *ctx, void *x, const void *b
  *     otherwise plain CG.  Stops when the normal-equation residual falls to
  *     params->tol (default 1e-8) relative to its right-hand side; info reports
  *     the true residual ||b - M x|| / ||b|| and, in n_reliable, the number of
- *     basis vectors now held.  FP64 throughout; Wilson operator (mu = 0).
+ *     basis vectors now held.  The CG iterations, H, the Galerkin guess and
+ *     all residuals are FP64; the search space (Lanczos vectors, restarts,
+ *     Ritz vectors) and the Gram-Schmidt of new basis vectors use FP32 copies
+ *     (they shape the subspace only; H is computed for the vectors stored).
+ *     Wilson operator (mu = 0).
  *   plq_eigcg_vectors: basis vectors held. */
 typedef struct plq_eigcg plq_eigcg;
 PLQ_API plq_status plq_eigcg_create(plq_ctx *ctx, int nev, int m, int max_vectors, plq_eigcg **out);

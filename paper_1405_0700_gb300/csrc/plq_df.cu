@@ -244,8 +244,8 @@ __global__ void split_kernel(long long N, float4 *out, const double2 *in) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const double2 a = in[(size_t)(2 * k) * N + e], b = in[(size_t)(2 * k + 1) * N + e];
-            const df ar = df_from_double(a.x), ai = df_from_double(a.y), br = df_from_double(b.x),
-                     bi = df_from_double(b.y);
+            const df ar = df_from_double_bits(a.x), ai = df_from_double_bits(a.y), br = df_from_double_bits(b.x),
+                     bi = df_from_double_bits(b.y);
             out[(size_t)k * N + e] = make_float4(ar.hi, ai.hi, br.hi, bi.hi);
             out[(size_t)(6 + k) * N + e] = make_float4(ar.lo, ai.lo, br.lo, bi.lo);
         }
@@ -257,8 +257,9 @@ __global__ void join_kernel(long long N, double2 *out, const float4 *in) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const float4 h = in[(size_t)k * N + e], l = in[(size_t)(6 + k) * N + e];
-            out[(size_t)(2 * k) * N + e] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
-            out[(size_t)(2 * k + 1) * N + e] = make_double2((double)h.z + (double)l.z, (double)h.w + (double)l.w);
+            out[(size_t)(2 * k) * N + e] = make_double2(df_to_double_bits({h.x, l.x}), df_to_double_bits({h.y, l.y}));
+            out[(size_t)(2 * k + 1) * N + e] =
+                make_double2(df_to_double_bits({h.z, l.z}), df_to_double_bits({h.w, l.w}));
         }
     }
 }

@@ -183,6 +183,51 @@ __global__ void accumulate_kernel(long long N, void *dst, const void *src) {
     }
 }
 
+// Per right-hand-side power-of-two scales of the mixed-precision solves.
+struct RhsScale {
+    double f[PLQ_MAX_RHS];
+};
+
+// f[r] by selects (run-time indexing would copy the array to local memory)
+__device__ __forceinline__ double scale_of(const RhsScale &S, long long e, int n) {
+    if (n == 1) return S.f[0];
+    const int r = (int)(e % n);
+    double v = S.f[0];
+#pragma unroll
+    for (int q = 1; q < PLQ_MAX_RHS; ++q) v = r == q ? S.f[q] : v;
+    return v;
+}
+
+// dst (FP64, n interleaved right-hand sides) *= f[rhs]
+__global__ void scale64_kernel(long long N, int n, double2 *v, RhsScale S) {
+    ELEM_LOOP(N) {
+        const double f = scale_of(S, e, n);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double2 a = v[(size_t)k * N + e];
+            v[(size_t)k * N + e] = make_double2(f * a.x, f * a.y);
+        }
+    }
+}
+
+// dst (FP64) += f[rhs] * src
+template <int PS>
+__global__ void accumulate_scaled_kernel(long long N, int n, void *dst, const void *src, RhsScale S) {
+    ELEM_LOOP(N) {
+        const double f = scale_of(S, e, n);
+        cx<RealOf<PS>> a[12];
+        cx<double> d[12];
+        Spinor<PS>::load(src, N, e, a);
+        Spinor<PLQ_F64>::load(dst, N, e, d);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            d[k].re = fma(f, (double)a[k].re, d[k].re);
+            d[k].im = fma(f, (double)a[k].im, d[k].im);
+        }
+        Spinor<PLQ_F64>::store(dst, N, e, d);
+    }
+}
+
 // dst = scale (1 + i nu gamma5) src
 template <int P>
 __global__ void twist_kernel(long long N, void *dst, const void *src, double nu, double scale) {
@@ -366,6 +411,24 @@ plq_status blas_cg_direction(long long N, int n, void *p, const void *r, int pre
 plq_status blas_accumulate(long long N, void *dst64, const void *src, int ps, cudaStream_t s) {
     const int grid = grid_for(N, false);
     DISPATCH_P(ps, accumulate_kernel, N, dst64, src);
+    PLQ_CUDA(cudaGetLastError());
+    return PLQ_OK;
+}
+
+plq_status blas_scale64(long long N, int n, void *v, const double *f, cudaStream_t s) {
+    RhsScale S{};
+    for (int r = 0; r < n && r < PLQ_MAX_RHS; ++r) S.f[r] = f[r];
+    scale64_kernel<<<grid_for(N, false), kBlock, 0, s>>>(N, n, static_cast<double2 *>(v), S);
+    PLQ_CUDA(cudaGetLastError());
+    return PLQ_OK;
+}
+
+plq_status blas_accumulate_scaled(long long N, int n, void *dst64, const void *src, int ps, const double *f,
+                                  cudaStream_t s) {
+    RhsScale S{};
+    for (int r = 0; r < n && r < PLQ_MAX_RHS; ++r) S.f[r] = f[r];
+    const int grid = grid_for(N, false);
+    DISPATCH_P(ps, accumulate_scaled_kernel, N, n, dst64, src, S);
     PLQ_CUDA(cudaGetLastError());
     return PLQ_OK;
 }

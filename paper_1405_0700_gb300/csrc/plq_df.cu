@@ -239,27 +239,48 @@ plq_status launch_df(const DfArgs &a, cudaStream_t s) {
 }
 
 // FP64 half field (12 planes of double2) <-> PLQ_DF64 half field, N elements
-__global__ void split_kernel(long long N, float4 *out, const double2 *in) {
+// (site * n + rhs); right-hand side r is scaled by 2^sh[r] on the way in and
+// by 2^-sh[r] on the way out.
+struct Shifts {
+    int sh[PLQ_MAX_RHS];
+};
+
+// sh[r] by selects (run-time indexing would copy the array to local memory)
+__device__ __forceinline__ int shift_of(const Shifts &S, long long e, int n) {
+    if (n == 1) return S.sh[0];
+    const int r = (int)(e % n);
+    int v = S.sh[0];
+#pragma unroll
+    for (int q = 1; q < PLQ_MAX_RHS; ++q) v = r == q ? S.sh[q] : v;
+    return v;
+}
+
+__global__ void split_kernel(long long N, int n, Shifts S, float4 *out, const double2 *in) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int es = shift_of(S, e, n);
+        const double sc = __longlong_as_double((long long)(es + 1023) << 52);  // 2^es
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const double2 a = in[(size_t)(2 * k) * N + e], b = in[(size_t)(2 * k + 1) * N + e];
-            const df ar = df_from_double_bits(a.x), ai = df_from_double_bits(a.y), br = df_from_double_bits(b.x),
-                     bi = df_from_double_bits(b.y);
+            const df ar = df_from_double_bits(a.x, es, sc), ai = df_from_double_bits(a.y, es, sc),
+                     br = df_from_double_bits(b.x, es, sc), bi = df_from_double_bits(b.y, es, sc);
             out[(size_t)k * N + e] = make_float4(ar.hi, ai.hi, br.hi, bi.hi);
             out[(size_t)(6 + k) * N + e] = make_float4(ar.lo, ai.lo, br.lo, bi.lo);
         }
     }
 }
 
-__global__ void join_kernel(long long N, double2 *out, const float4 *in) {
+__global__ void join_kernel(long long N, int n, Shifts S, double2 *out, const float4 *in) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int es = -shift_of(S, e, n);
+        const double sc = __longlong_as_double((long long)(es + 1023) << 52);  // 2^es
+        // float -> double conversions are exact; one FP64 add and multiply each
+        auto join = [sc](float h, float l) { return ((double)h + (double)l) * sc; };
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
             const float4 h = in[(size_t)k * N + e], l = in[(size_t)(6 + k) * N + e];
-            out[(size_t)(2 * k) * N + e] = make_double2(df_to_double_bits({h.x, l.x}), df_to_double_bits({h.y, l.y}));
-            out[(size_t)(2 * k + 1) * N + e] =
-                make_double2(df_to_double_bits({h.z, l.z}), df_to_double_bits({h.w, l.w}));
+            out[(size_t)(2 * k) * N + e] = make_double2(join(h.x, l.x), join(h.y, l.y));
+            out[(size_t)(2 * k + 1) * N + e] = make_double2(join(h.z, l.z), join(h.w, l.w));
         }
     }
 }
@@ -395,14 +416,18 @@ plq_status df_unpack_spinor(const Lattice &L, double *out, const void *in, int n
     return PLQ_OK;
 }
 
-plq_status df_split(long long N, void *out, const void *in, cudaStream_t s) {
-    split_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, static_cast<float4 *>(out), static_cast<const double2 *>(in));
+plq_status df_split(long long N, int n, const int *shifts, void *out, const void *in, cudaStream_t s) {
+    Shifts S{};
+    for (int r = 0; r < n && r < PLQ_MAX_RHS; ++r) S.sh[r] = shifts ? shifts[r] : 0;
+    split_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, n, S, static_cast<float4 *>(out), static_cast<const double2 *>(in));
     PLQ_CUDA(cudaGetLastError());
     return PLQ_OK;
 }
 
-plq_status df_join(long long N, void *out, const void *in, cudaStream_t s) {
-    join_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, static_cast<double2 *>(out), static_cast<const float4 *>(in));
+plq_status df_join(long long N, int n, const int *shifts, void *out, const void *in, cudaStream_t s) {
+    Shifts S{};
+    for (int r = 0; r < n && r < PLQ_MAX_RHS; ++r) S.sh[r] = shifts ? shifts[r] : 0;
+    join_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, n, S, static_cast<double2 *>(out), static_cast<const float4 *>(in));
     PLQ_CUDA(cudaGetLastError());
     return PLQ_OK;
 }

@@ -63,39 +63,28 @@ __device__ __forceinline__ df df_from_double(double d) {
 }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
-// The same split from the bit fields, for the bulk conversion kernels: a
-// double <-> float conversion issues on this GPU's FP64 pipe (as slow as an
-// FP64 add), integer and FP32 operations do not.  hi keeps the sign, the
-// exponent and the top 23 mantissa bits of d (truncated); lo is the
-// remaining 29-bit tail rounded to a float, so hi + lo = d to 2^-48 |d| and
-// |lo| < ulp(hi).  Values outside the normal FP32 exponent range (zero,
-// |d| < 2^-126, |d| >= 2^128, Inf, NaN) take the conversion path.
-__device__ __forceinline__ df df_from_double_bits(double d) {
+// The same split of d * 2^es from the bit fields, for the bulk conversion
+// kernels: a double -> float conversion issues on this GPU's FP64 pipe (as
+// slow as an FP64 add), integer and FP32 operations do not.  hi keeps the
+// sign, the (shifted) exponent and the top 23 mantissa bits of d
+// (truncated); lo is the remaining 29-bit tail rounded to a float, so
+// hi + lo = d 2^es to 2^-48 |d 2^es| and |lo| < ulp(hi).  The power-of-two
+// shift lets callers bring fields of any magnitude into the FP32 exponent
+// range; values still outside it (Inf, NaN, extreme exponents) take the
+// conversion path, with sc = 2^es as a double.
+__device__ __forceinline__ df df_from_double_bits(double d, int es, double sc) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    const int fe = (int)((b >> 52) & 0x7ff) - 1023 + 127;  // FP32 biased exponent
-    if (fe < 1 || fe > 254) return df_from_double(d);
+    const int de = (int)((b >> 52) & 0x7ff);
+    const int fe = de - 1023 + 127 + es;  // FP32 biased exponent of d 2^es
+    if ((b << 1) == 0ull) return {__uint_as_float(sign), 0.f};  // +-0
+    if (de == 0 || de == 0x7ff || fe < 1 || fe > 254) return df_from_double(d * sc);
     const unsigned long long m = b & 0xfffffffffffffull;
     const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)(m >> 29));
     // tail * 2^(e - 52) = tail * 2^-52 * 2^(fe - 127); each factor is a normal float
     float lo = __fmul_rn(__uint2float_rn((unsigned)(m & 0x1fffffffu)), 2.220446049250313e-16f);
     lo = __fmul_rn(lo, __uint_as_float((unsigned)fe << 23));
     return {hi, __uint_as_float(__float_as_uint(lo) | sign)};
-}
-
-// Exact double of a normal float from its bit fields (zero, subnormal, Inf
-// and NaN take the conversion path).
-__device__ __forceinline__ double double_of_float_bits(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned fe = (u >> 23) & 0xffu;
-    if (fe == 0u || fe == 255u) return (double)f;
-    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                 ((unsigned long long)(fe - 127u + 1023u) << 52) |
-                                 ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)b);
-}
-__device__ __forceinline__ double df_to_double_bits(df a) {
-    return double_of_float_bits(a.hi) + double_of_float_bits(a.lo);
 }
 
 // Accumulator of a sum of products: s collects the high parts through TwoSum,

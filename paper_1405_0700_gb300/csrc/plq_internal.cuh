@@ -217,9 +217,11 @@ size_t df_site_bytes();
 plq_status df_gauge_upload(struct plq_ctx *c, const double *U, int is_device, int link_reals, cudaStream_t s);
 plq_status df_pack_spinor(const Lattice &L, void *out, const double *in, int nrhs, cudaStream_t s);
 plq_status df_unpack_spinor(const Lattice &L, double *out, const void *in, int nrhs, cudaStream_t s);
-// FP64 half field of N elements <-> PLQ_DF64 half field
-plq_status df_split(long long N, void *out, const void *in, cudaStream_t s);
-plq_status df_join(long long N, void *out, const void *in, cudaStream_t s);
+// FP64 half field of N = Vh * n elements <-> PLQ_DF64 half field; right-hand
+// side r is scaled by 2^shifts[r] into the float-float field and back
+// (shifts may be null: no scaling)
+plq_status df_split(long long N, int n, const int *shifts, void *out, const void *in, cudaStream_t s);
+plq_status df_join(long long N, int n, const int *shifts, void *out, const void *in, cudaStream_t s);
 // out = scale_h (1 + i nu_h gamma5) H in, or with x: out = x + a * that (all PLQ_DF64)
 plq_status df_hop(const struct plq_ctx *c, int out_parity, void *out, const void *in, const void *x, double a,
                   double nu_h, double scale_h, int nrhs, cudaStream_t s);
@@ -246,6 +248,10 @@ plq_status blas_cg_direction(long long N, int n, void *p, const void *r, int pre
                              cudaStream_t s);
 // dst(F64) += convert(src)
 plq_status blas_accumulate(long long N, void *dst64, const void *src, int psrc, cudaStream_t s);
+// v (FP64, n interleaved right-hand sides) *= f[r];  dst64 += f[r] * src
+plq_status blas_scale64(long long N, int n, void *v, const double *f, cudaStream_t s);
+plq_status blas_accumulate_scaled(long long N, int n, void *dst64, const void *src, int psrc, const double *f,
+                                  cudaStream_t s);
 // dst = scale * (1 + i nu gamma5) src (same precision, may alias)
 plq_status blas_twist(long long N, void *dst, const void *src, int prec, double nu, double scale, cudaStream_t s);
 // y = x + a * y (FP64, host scalar)

@@ -86,17 +86,21 @@ plq_status true_residual(Solve &S, void *s64, void *tmp_o64, const void *bhat, c
 // The same residual with both half-applications in float-float arithmetic
 // (PLQ_DF64): x_e and bhat - A x_e are split into float-float fields (dfe,
 // even), the odd intermediate lives in dfo; s is joined back into FP64 for
-// the norm and the restart.  A x_e and bhat - A x_e stay FP64.
-plq_status true_residual_df(Solve &S, void *s64, void *dfo, void *dfe, const void *bhat, const void *xe, double *s2) {
+// the norm and the restart.  A x_e and bhat - A x_e stay FP64.  sh[r] scales
+// right-hand side r by a power of two (the inverse of its source norm) so
+// that the float-float fields sit in the FP32 exponent range whatever the
+// magnitude of the source; the operator is linear, the join undoes it.
+plq_status true_residual_df(Solve &S, const int *sh, void *s64, void *dfo, void *dfe, const void *bhat, const void *xe,
+                            double *s2) {
     const Tw t1 = tw_first(S, false);
-    PLQ_TRY(df_split(S.N, dfe, xe, S.s));
+    PLQ_TRY(df_split(S.N, S.n, sh, dfe, xe, S.s));
     PLQ_TRY(df_hop(S.c, 1, dfo, dfe, nullptr, 0.0, t1.nu_h, t1.scale_h, S.n, S.s));
     if (S.nu != 0.0) PLQ_TRY(blas_twist(S.N, s64, xe, PLQ_F64, S.nu, 1.0, S.s));
     else PLQ_TRY(blas_copy_convert(S.N, s64, PLQ_F64, xe, PLQ_F64, S.s));
     PLQ_TRY(blas_xpay64(S.N, bhat, -1.0, s64, S.s));
-    PLQ_TRY(df_split(S.N, dfe, s64, S.s));
+    PLQ_TRY(df_split(S.N, S.n, sh, dfe, s64, S.s));
     PLQ_TRY(df_hop(S.c, 0, dfe, dfo, dfe, S.kappa * S.kappa, 0.0, 1.0, S.n, S.s));
-    PLQ_TRY(df_join(S.N, s64, dfe, S.s));
+    PLQ_TRY(df_join(S.N, S.n, sh, s64, dfe, S.s));
     S.hops += 2;
     return norm2_64(S, s64, s2);
 }
@@ -216,6 +220,22 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
                 }
             }
         }
+        // Right-hand side r is scaled by 2^-(exponent of |b_r|) wherever it enters a
+        // narrower format -- the float-float fields and the inner (FP32/FP16)
+        // iteration -- so that sources of any magnitude sit in their exponent
+        // range (an FP32 residual of a 1e-45 source would flush to zero).  The
+        // scale is fixed for the whole solve, so the kept direction p and the
+        // inner scalars stay consistent across reliable updates.
+        std::vector<int> dfsh(n, 0);
+        std::vector<double> isc(n, 1.0), sc(n, 1.0);
+        for (int r = 0; r < n; ++r)
+            if (bnorm[r] > 0.0 && std::isfinite(bnorm[r])) {
+                dfsh[r] = -std::ilogb(bnorm[r]);
+                if (S.P != PLQ_F64) {
+                    sc[r] = std::ldexp(1.0, dfsh[r]);
+                    isc[r] = std::ldexp(1.0, -dfsh[r]);
+                }
+            }
         // bhat = b_e + kappa H_eo A^{-1} b_o (A = 1 for Wilson)
         const void *bsrc = bo;
         if (S.nu != 0.0) {  // (r64 is free until the iteration starts)
@@ -223,10 +243,10 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
             bsrc = r64;
         }
         if (df_res) {  // in float-float: t64 / tmp_o64 hold the split fields
-            if ((st = df_split(S.N, tmp_o64, bsrc, s)) != PLQ_OK) break;
-            if ((st = df_split(S.N, t64, be, s)) != PLQ_OK) break;
+            if ((st = df_split(S.N, n, dfsh.data(), tmp_o64, bsrc, s)) != PLQ_OK) break;
+            if ((st = df_split(S.N, n, dfsh.data(), t64, be, s)) != PLQ_OK) break;
             if ((st = df_hop(c, 0, t64, tmp_o64, t64, kappa, 0.0, 1.0, n, s)) != PLQ_OK) break;
-            if ((st = df_join(S.N, bhat, t64, s)) != PLQ_OK) break;
+            if ((st = df_join(S.N, n, dfsh.data(), bhat, t64, s)) != PLQ_OK) break;
             S.hops += 1;
         } else if ((st = hop(S, PLQ_F64, 0, bhat, bsrc, EPI_XPAY, 0, be, kappa)) != PLQ_OK) {
             break;
@@ -235,7 +255,7 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
         const double delta = S.P == PLQ_F64 ? 0.0 : P.delta;
         for (;;) {
             // (t64 is free until the final check; it holds the float-float fields)
-            st = df_res ? true_residual_df(S, s64, tmp_o64, t64, bhat, xe, s2.data())
+            st = df_res ? true_residual_df(S, dfsh.data(), s64, tmp_o64, t64, bhat, xe, s2.data())
                         : true_residual(S, s64, tmp_o64, bhat, xe, s2.data());
             if (st != PLQ_OK) break;
             bool all_done = true;
@@ -292,6 +312,7 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
                     if ((st = blas_copy_convert(S.N, rL, S.P, r64, PLQ_F64, s)) != PLQ_OK) break;
                 } else {
                     void *sL = mpL;  // free until the inner iteration starts
+                    if ((st = blas_scale64(S.N, n, s64, sc.data(), s)) != PLQ_OK) break;
                     if ((st = blas_copy_convert(S.N, sL, S.P, s64, PLQ_F64, s)) != PLQ_OK) break;
                     if ((st = hop(S, S.P, 1, toL, sL, EPI_PLAIN, 1, nullptr, 0.0, FIN_NONE, nullptr, false,
                                   tw_first(S, true))) != PLQ_OK)
@@ -333,15 +354,17 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
                 if ((st = run_batches(S, P.k, body, fin, &c->solve_graph[method], gkey)) != PLQ_OK) break;
             } else {
                 void *rL = L[0], *rhL = L[1], *pL = L[2], *vL = L[3], *sL = L[4], *tL = L[5], *toL = L[6];
+                if ((st = blas_scale64(S.N, n, s64, sc.data(), s)) != PLQ_OK) break;
                 if ((st = blas_copy_convert(S.N, rL, S.P, s64, PLQ_F64, s)) != PLQ_OK) break;
                 if ((st = blas_copy_convert(S.N, rhL, S.P, rL, S.P, s)) != PLQ_OK) break;
                 if ((st = blas_copy_convert(S.N, pL, S.P, rL, S.P, s)) != PLQ_OK) break;
                 if ((st = blas_zero(S.N, xL, S.PX, s)) != PLQ_OK) break;
                 for (int r = 0; r < n; ++r) {
                     if (done[r]) continue;
-                    target2[r] = std::pow(sigma[r] * P.tol * bnorm[r], 2);
-                    init[r].c_rho = make_double2(s2[r], 0.0);
-                    init[r].stop_r2 = std::fmax(delta * delta * s2[r], target2[r]);
+                    // (inner quantities carry the factor sc[r])
+                    target2[r] = std::pow(sigma[r] * P.tol * bnorm[r] * sc[r], 2);
+                    init[r].c_rho = make_double2(s2[r] * sc[r] * sc[r], 0.0);
+                    init[r].stop_r2 = std::fmax(delta * delta * s2[r] * sc[r] * sc[r], target2[r]);
                     init[r].tiny = 1e-300;
                 }
                 if ((st = put_states(S, init)) != PLQ_OK) break;
@@ -383,16 +406,16 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
                 last_rho[r] = fin[r].beta > 0.0 ? fin[r].rho / fin[r].beta : fin[r].rho;
             }
             // reliable update: x_e += x_inner (FP64); frozen right-hand sides add zero
-            if ((st = blas_accumulate(S.N, xe, xL, S.PX, s)) != PLQ_OK) break;
+            if ((st = blas_accumulate_scaled(S.N, n, xe, xL, S.PX, isc.data(), s)) != PLQ_OK) break;
             first = false;
         }
         if (st != PLQ_OK) break;
         // x_o = A^{-1} (b_o + kappa H_oe x_e)
         if (df_res) {
-            if ((st = df_split(S.N, t64, xe, s)) != PLQ_OK) break;
-            if ((st = df_split(S.N, tmp_o64, bo, s)) != PLQ_OK) break;
+            if ((st = df_split(S.N, n, dfsh.data(), t64, xe, s)) != PLQ_OK) break;
+            if ((st = df_split(S.N, n, dfsh.data(), tmp_o64, bo, s)) != PLQ_OK) break;
             if ((st = df_hop(c, 1, tmp_o64, t64, tmp_o64, kappa, 0.0, 1.0, n, s)) != PLQ_OK) break;
-            if ((st = df_join(S.N, xo, tmp_o64, s)) != PLQ_OK) break;
+            if ((st = df_join(S.N, n, dfsh.data(), xo, tmp_o64, s)) != PLQ_OK) break;
             S.hops += 1;
         } else if ((st = hop(S, PLQ_F64, 1, xo, xe, EPI_XPAY, 0, bo, kappa)) != PLQ_OK) {
             break;

@@ -164,3 +164,28 @@ def test_multi_rhs_point_sources_with_float_float_residuals():
     for r in range(12):
         res = float(np.linalg.norm(b[r] - C.wilson(U, x[r], kappa)) / np.linalg.norm(b[r]))
         assert res <= 1e-10, (r, res, infos[r].as_dict())
+
+
+@pytest.mark.parametrize("scale", [1e-45, 1e-30, 1e30])
+@pytest.mark.parametrize("residual_prec", [F64, DF64])
+@pytest.mark.parametrize("method", ["cg", "bicgstab"])
+def test_mixed_solves_for_any_source_magnitude(scale, residual_prec, method):
+    """The inner (FP32) iteration and the float-float fields see each right-hand
+    side scaled by a power of two, so sources far outside the FP32 exponent range
+    solve as well as O(1) ones."""
+    dims = (8, 4, 4, 8)
+    kappa = 0.12
+    U, b = S.gauge_and_spinor(dims, 0.3, 8)
+    b = b * scale
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        ctx.gauge_upload(U, 18, DF64)
+        bd = ctx.to_device(b, F64)
+        x = ctx.empty_full(F64)
+        fn = ctx.cg_solve if method == "cg" else ctx.bicgstab_solve
+        info = fn(x, bd, kappa, inner_prec=F32, residual_prec=residual_prec)
+        xs = ctx.to_host(x, F64)
+    res = float(np.linalg.norm(b - C.wilson(U, xs, kappa)) / np.linalg.norm(b))
+    assert res <= 1e-10, (scale, res, info.as_dict())
+    assert abs(info.true_rel_residual - res) < 1e-11

@@ -35,6 +35,7 @@ struct BatchSystem {
     size_t gbL;
     const void *be, *bo;
     void *xe, *xo;
+    int inner_scaled;  // 1: scale the inner iteration (FP32 / FP16 inner precision)
     void *bhat, *s64, *to64;           // FP64 half fields (to64: odd)
     void *rL, *pL, *qL, *mpL, *toL;    // inner half fields (toL: odd)
     void *xL;                          // inner solution accumulator (FP32 or FP64)
@@ -70,6 +71,7 @@ enum { BF_NAN = 1, BF_NOT_CONVERGED = 2 };
 struct SysRun {
     int mode, iter, nrel, first, flags, reduces;
     double b2, s2, r2, rho, alpha, beta, last_rho, stop_r2, target2, sigma;
+    double sc;  // power of two applied where the residual enters the inner precision
 };
 
 struct BatchArgs {
@@ -300,7 +302,7 @@ __device__ double run_site(int mode, const BatchSystem &B, const SysRun &R, int 
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             acc[k] = {fma(kk, acc[k].re, bh[k].re - x[k].re), fma(kk, acc[k].im, bh[k].im - x[k].im)};
-            sl[k] = {(T)acc[k].re, (T)acc[k].im};
+            sl[k] = {(T)(R.sc * acc[k].re), (T)(R.sc * acc[k].im)};
         }
         st<PLQ_F64>(B.s64, Vh, i, acc);
         st<PL>(B.mpL, Vh, i, sl);  // mpL is free until the inner iteration starts
@@ -392,8 +394,10 @@ __device__ double run_site(int mode, const BatchSystem &B, const SysRun &R, int 
         cx<RealOf<PX>> xl[12];
         ld<PLQ_F64>(B.xe, Vh, i, x);
         ld<PX>(B.xL, Vh, i, xl);
+        const double isc = 1.0 / R.sc;  // exact: R.sc is a power of two
 #pragma unroll
-        for (int k = 0; k < 12; ++k) x[k] = {x[k].re + (double)xl[k].re, x[k].im + (double)xl[k].im};
+        for (int k = 0; k < 12; ++k)
+            x[k] = {fma(isc, (double)xl[k].re, x[k].re), fma(isc, (double)xl[k].im, x[k].im)};
         st<PLQ_F64>(B.xe, Vh, i, x);
         return 0.0;
     }
@@ -422,6 +426,9 @@ __device__ void advance(SysRun &R, const BatchSystem &B, double v) {
         R.b2 = v;
         if (!isfinite(v)) { R.flags |= BF_NAN; R.mode = M_DONE; }
         else R.mode = (v == 0.0) ? M_ZERO : M_SETUP1;
+        // inner quantities carry 2^-(exponent of |b|), so that sources of any
+        // magnitude sit in the inner precision's exponent range
+        if (isfinite(v) && v > 0.0 && B.inner_scaled) R.sc = ldexp(1.0, -ilogb(sqrt(v)));
         break;
     case M_SETUP1: R.mode = M_RES1; break;
     case M_RES1: R.mode = M_RES2; break;
@@ -491,6 +498,7 @@ __global__ void __launch_bounds__(128, 4) batched_cg_kernel(BatchArgs a) {
         R.first = 1;
         R.b2 = R.s2 = R.r2 = R.rho = R.alpha = R.beta = R.last_rho = R.stop_r2 = R.target2 = 0.0;
         R.sigma = 0.5;
+        R.sc = 1.0;
         run[s] = R;
     }
     __syncthreads();
@@ -656,6 +664,7 @@ extern "C" plq_status plq_cg_solve_batched(plq_ctx **ctxs, int n, void **x, cons
         B.gb64 = c->gauge[PLQ_F64].block;
         B.gL = c->gauge[inner].ptr;
         B.gbL = c->gauge[inner].block;
+        B.inner_scaled = inner != PLQ_F64;
         B.be = b[k];
         B.bo = static_cast<const char *>(b[k]) + h64;
         B.xe = x[k];

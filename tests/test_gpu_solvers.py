@@ -229,6 +229,33 @@ def test_batched_uneven_systems_one_launch():
         c.close()
 
 
+def test_batched_sources_of_any_magnitude():
+    """Systems whose sources lie far outside the FP32 exponent range, in one
+    persistent launch with an FP32 inner iteration (each system's inner
+    quantities are scaled by a power of two)."""
+    from paper_1405_0700_gb300 import plq as P
+
+    dims = (8, 4, 4, 4)
+    ctxs, xs, bs, Us, srcs = [], [], [], [], []
+    for k, scale in enumerate((1e-45, 1.0, 1e30)):
+        U, b = S.gauge_and_spinor(dims, 0.3, 70 + k)
+        b = b * scale
+        ctx = Context(dims)
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        ctxs.append(ctx)
+        bs.append(ctx.to_device(b, F64))
+        xs.append(ctx.empty_full(F64))
+        Us.append(U)
+        srcs.append(b)
+    infos, _ = P.cg_solve_batched(ctxs, xs, bs, [0.12] * 3, inner_prec=F32)
+    for k in range(3):
+        res = oracle_residual(Us[k], srcs[k], ctxs[k].to_host(xs[k], F64), 0.12)
+        assert res <= 1e-10, (k, res, infos[k].as_dict())
+    for c in ctxs:
+        c.close()
+
+
 @pytest.mark.parametrize("inner", [F64, F16])
 def test_batched_inner_precisions(inner):
     from paper_1405_0700_gb300 import plq as P

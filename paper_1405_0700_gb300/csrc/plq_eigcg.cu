@@ -194,10 +194,12 @@ __global__ void lincomb32_kernel(long long N, const float2 *in, size_t stride, i
     }
 }
 
-__global__ void to32_kernel(long long N, float2 *out, const double2 *in) {
+// out = f * in in FP32 (f a power of two that brings the field into the FP32
+// exponent range)
+__global__ void to32_kernel(long long N, float2 *out, const double2 *in, double f) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
         const double2 a = in[e];
-        out[e] = make_float2((float)a.x, (float)a.y);
+        out[e] = make_float2((float)(f * a.x), (float)(f * a.y));
     }
 }
 
@@ -535,14 +537,17 @@ extern "C" plq_status plq_eigcg_solve(plq_eigcg *E, void *x, const void *b, doub
         double rho0 = 0;
         if ((st = norm2_64(G.S, r, &rho0)) != PLQ_OK) break;
         const bool eig = accumulate && E->nvec < E->max_vectors;
+        // the raw residuals r_j go into the FP32 search space scaled by 2^-(exponent
+        // of |r_0|) (and their norms in nrm with them), whatever the source magnitude
+        const double vscale = rho0 > 0.0 && std::isfinite(rho0) ? std::ldexp(1.0, -std::ilogb(std::sqrt(rho0))) : 1.0;
         const int m = E->m, nev = E->nev, k2 = 2 * nev;
         // search space bookkeeping (host): raw vectors in V, their norms, T
         std::vector<double> T((size_t)(m + 1) * (m + 1), 0.0), nrm(m + 1, 1.0);
         int vs = 1;  // V slot 0 holds r_0 (raw)
         if (eig) {
-            to32_kernel<<<grid_of(G.N, false), 256, 0, s>>>(G.N, E->V, static_cast<const double2 *>(r));
+            to32_kernel<<<grid_of(G.N, false), 256, 0, s>>>(G.N, E->V, static_cast<const double2 *>(r), vscale);
             PLQ_CUDA(cudaGetLastError());
-            nrm[0] = std::sqrt(rho0);
+            nrm[0] = vscale * std::sqrt(rho0);
         }
         double alpha_prev = 0, beta_prev = 0;
         bool have_prev = false;
@@ -571,7 +576,7 @@ extern "C" plq_status plq_eigcg_solve(plq_eigcg *E, void *x, const void *b, doub
                 PLQ_TRY(blas_cg_update(G.S.N, 1, xe, r, p, q, PLQ_F64, rb, c->state, s));
                 if (eig) {  // raw r_{j+1} into its (FP32) slot of the search space
                     to32_kernel<<<grid_of(G.N, false), 256, 0, s>>>(G.N, Vb + (size_t)(vs + i) * E->slot,
-                                                                    static_cast<const double2 *>(r));
+                                                                    static_cast<const double2 *>(r), vscale);
                     PLQ_CUDA(cudaGetLastError());
                 }
                 return blas_cg_direction(G.S.N, 1, p, r, PLQ_F64, c->state, s);
@@ -614,7 +619,7 @@ extern "C" plq_status plq_eigcg_solve(plq_eigcg *E, void *x, const void *b, doub
                     if (sl + 1 <= m) {
                         T[(size_t)sl * (m + 1) + sl + 1] = off;
                         T[(size_t)(sl + 1) * (m + 1) + sl] = off;
-                        nrm[sl + 1] = std::sqrt(rn);
+                        nrm[sl + 1] = vscale * std::sqrt(rn);
                     }
                     alpha_prev = al;
                     beta_prev = be2;

@@ -72,3 +72,24 @@ def test_eigcg_rejects_bad_parameters():
     with Context((4, 4, 4, 4)) as ctx:
         with pytest.raises(PLQError):
             EigCG(ctx, nev=10, m=12)  # m < 2 nev + 2
+
+
+def test_eigcg_accumulates_for_tiny_sources():
+    # the FP32 search space is scaled by a power of two: a source of norm ~1e-40
+    # still yields the nev new basis vectors per accumulating solve
+    dims = (16, 4, 4, 4)
+    kappa = 0.1255
+    U = S.gauge_field(dims, 0.05, 91)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        eig = EigCG(ctx, nev=8, m=24, max_vectors=24)
+        for k in range(3):
+            b = S.gaussian_spinor(dims, 400 + k) * 1e-40
+            bd = ctx.to_device(b, F64)
+            x = ctx.empty_full(F64)
+            info = eig.solve(x, bd, kappa, tol=1e-10, accumulate=True)
+            xs = ctx.to_host(x, F64)
+            res = np.linalg.norm(b - C.wilson(U, xs, kappa)) / np.linalg.norm(b)
+            assert res < 1e-7, (k, res)
+        assert eig.vectors == 24
+        eig.close()

@@ -8,10 +8,11 @@
 // splits every double d exactly into hi = rn(d), lo = rn(d - hi).
 //
 // Operator.  The same Eq. (1) as every other precision, through the half
-// spinors of Eq. (2): projection and reconstruction with renormalised
-// float-float additions; each SU(3) x half-spinor row as one sum of six
-// products whose high parts are added by TwoSum and whose rounding errors and
-// low-order terms are gathered in one float (renormalised once per row).
+// spinors of Eq. (2): projection and reconstruction with float-float
+// additions whose low parts are renormalised once per site; each SU(3) x
+// half-spinor row as one sum of six products whose high parts are added by
+// TwoSum and whose rounding errors and low-order terms are gathered in one
+// float (renormalised once per row).
 //
 // Used by the mixed-precision solvers for the reliable-update residual
 // s = bhat - Mhat x (two half-applications), where the FP64 operator would
@@ -156,8 +157,9 @@ __device__ __forceinline__ void hop_dir_df(const DfArgs &a, const SiteGeom &g, i
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const cx<df> a0 = p2 ? phi[6 + c] : phi[9 + c], a1 = p2 ? phi[9 + c] : phi[6 + c];
-        h[c] = cadd(phi[c], mul_ipow_rt(a0, k0));
-        h[3 + c] = cadd(phi[3 + c], mul_ipow_rt(a1, k1));
+        const cx<df> b0 = mul_ipow_rt(a0, k0), b1 = mul_ipow_rt(a1, k1);
+        h[c] = {add_lazy(phi[c].re, b0.re), add_lazy(phi[c].im, b0.im)};
+        h[3 + c] = {add_lazy(phi[3 + c].re, b1.re), add_lazy(phi[3 + c].im, b1.im)};
     }
     if (flip) {
 #pragma unroll
@@ -168,11 +170,12 @@ __device__ __forceinline__ void hop_dir_df(const DfArgs &a, const SiteGeom &g, i
     const int j0 = (4 - k0) & 3, j1 = (4 - k1) & 3;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        acc[c] = cadd(acc[c], uh[c]);
-        acc[3 + c] = cadd(acc[3 + c], uh[3 + c]);
+        auto acc_add = [](cx<df> &a, cx<df> v) { a = {add_lazy(a.re, v.re), add_lazy(a.im, v.im)}; };
+        acc_add(acc[c], uh[c]);
+        acc_add(acc[3 + c], uh[3 + c]);
         const cx<df> l0 = mul_ipow_rt(uh[c], j0), l1 = mul_ipow_rt(uh[3 + c], j1);
-        acc[6 + c] = cadd(acc[6 + c], p2 ? l0 : l1);
-        acc[9 + c] = cadd(acc[9 + c], p2 ? l1 : l0);
+        acc_add(acc[6 + c], p2 ? l0 : l1);
+        acc_add(acc[9 + c], p2 ? l1 : l0);
     }
 }
 
@@ -194,6 +197,8 @@ __global__ void __launch_bounds__(128) hop_df_kernel(const DfArgs a) {
         for (int k = 0; k < 12; ++k) acc[k] = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 1
         for (int d = 0; d < 8; ++d) hop_dir_df(a, g, i, r, d, acc);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = {renorm(acc[k].re), renorm(acc[k].im)};
         if (twist) {  // scale * (1 + i g nu) acc, g = +1 (upper spins) / -1 (lower)
 #pragma unroll
             for (int k = 0; k < 12; ++k) {

@@ -45,6 +45,16 @@ __device__ __forceinline__ df operator+(df a, df b) {
     return t;
 }
 __device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
+
+// a + b without the final renormalisation: the error of the high parts and
+// both low parts go into lo (8 operations instead of 14).  |lo| may grow to a
+// few ulp(hi); sums of a handful of terms stay accurate to ~2^-48 of their
+// inputs, and renorm() restores |lo| <= ulp(hi)/2.
+__device__ __forceinline__ df add_lazy(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ df renorm(df a) { return two_sum(a.hi, a.lo); }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
 
 // a * b (the lo * lo term is below the format's precision)

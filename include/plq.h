@@ -60,6 +60,10 @@
  * stream).  Operator calls are asynchronous on that stream.  Solver calls
  * synchronise it before they return because they fill plq_solve_info.
  *
+ * Threads: entry points may be called from any host thread.  Calls that use
+ * the same context (its gauge copies, workspace, tuning table and solver
+ * graphs) must not overlap; different contexts may be used concurrently.
+ *
  * Errors: every function returns PLQ_OK (0) or an error code; the matching
  * message is available from plq_last_error() in the calling thread.  No entry
  * point traps on the device, asserts, or throws across the ABI.  Invalid

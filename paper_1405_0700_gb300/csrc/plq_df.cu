@@ -17,6 +17,8 @@
 // Used by the mixed-precision solvers for the reliable-update residual
 // s = bhat - Mhat x (two half-applications), where the FP64 operator would
 // otherwise dominate the solve time on this GPU.
+#include <atomic>
+
 #include "plq_df.cuh"
 #include "plq_hop_impl.cuh"
 
@@ -226,16 +228,16 @@ int sm_count() {
 
 template <bool XPAY>
 plq_status launch_df(const DfArgs &a, cudaStream_t s) {
-    static int per_sm = 0;
+    static std::atomic<int> per_sm{0};  // occupancy, filled on first use
     const int block = 128;
-    if (per_sm == 0) {
+    if (per_sm.load(std::memory_order_relaxed) == 0) {
         int nb = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hop_df_kernel<XPAY>, block, 0);
         if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(hop_df)");
-        per_sm = nb > 0 ? nb : 1;
+        per_sm.store(nb > 0 ? nb : 1, std::memory_order_relaxed);
     }
     const long long total = (long long)a.lat.Vh * a.nrhs;
-    const long long want = (total + block - 1) / block, cap = (long long)per_sm * sm_count();
+    const long long want = (total + block - 1) / block, cap = (long long)per_sm.load(std::memory_order_relaxed) * sm_count();
     const int grid = (int)(want < cap ? want : cap);
     if (grid <= 0) return PLQ_OK;
     hop_df_kernel<XPAY><<<grid, block, 0, s>>>(a);

@@ -21,6 +21,8 @@
 // (1 + gamma_mu) flips the sign of c.  c is stored as a power of i.
 #pragma once
 
+#include <atomic>
+
 #include "plq_fields.cuh"
 
 namespace plq {
@@ -516,19 +518,19 @@ plq_status launch_mrhs_t(const HopArgs &a, cudaStream_t s, int block) {
             break;
         }
     const int threads = tiles * spb;
-    static int per_sm[257] = {0};
+    static std::atomic<int> per_sm[257];  // occupancy per block size, filled on first use
     auto kern = hop_mrhs_kernel<P, R, EPI, DAG, RT>;
-    if (per_sm[threads] == 0) {
+    if (per_sm[threads].load(std::memory_order_relaxed) == 0) {
         int nb = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0);
         if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(hop_mrhs)");
-        per_sm[threads] = nb > 0 ? nb : 1;
+        per_sm[threads].store(nb > 0 ? nb : 1, std::memory_order_relaxed);
     }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long want = ((long long)a.lat.Vh + spb - 1) / spb;
-    long long cap = (long long)per_sm[threads] * sms;
+    long long cap = (long long)per_sm[threads].load(std::memory_order_relaxed) * sms;
     if (EPI >= EPI_XPAY_NORM && cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
     const int grid = (int)(want < cap ? want : cap);
     if (grid <= 0) return PLQ_OK;
@@ -569,24 +571,24 @@ plq_status launch_hop_t(const HopArgs &a, cudaStream_t s, int block) {
             break;
         }
     const int threads = tiles * spb;
-    static int per_sm[257] = {0};
+    static std::atomic<int> per_sm[257];  // occupancy per block size, filled on first use
     constexpr int nreg = hop_reg_cap<P, R, EPI, TBL, RT>();
     auto kern = [] {
         if constexpr (nreg > 0) return hop_kernel_capped<P, R, EPI, DAG, TBL, RT, (nreg > 0 ? nreg : 255)>;
         else return hop_kernel<P, R, EPI, DAG, TBL, RT>;
     }();
-    if (per_sm[threads] == 0) {
+    if (per_sm[threads].load(std::memory_order_relaxed) == 0) {
         int nb = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0);
         if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(hop)");
-        per_sm[threads] = nb > 0 ? nb : 1;
+        per_sm[threads].store(nb > 0 ? nb : 1, std::memory_order_relaxed);
     }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int i_end = a.site_end < 0 ? a.lat.Vh : a.site_end;
     long long want = ((long long)(i_end - a.site_begin) + spb - 1) / spb;
-    long long cap = (long long)per_sm[threads] * sms;
+    long long cap = (long long)per_sm[threads].load(std::memory_order_relaxed) * sms;
     if (EPI >= EPI_XPAY_NORM && cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
     const int grid = (int)(want < cap ? want : cap);
     if (grid <= 0) return PLQ_OK;

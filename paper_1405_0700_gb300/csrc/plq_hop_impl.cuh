@@ -356,7 +356,7 @@ template <int P, int R, int EPI, bool DAG, int RT>
 __global__ void __launch_bounds__(256) hop_mrhs_kernel(const HopArgs a) {
     using T = RealOf<P>;
     __shared__ cx<T> sU[kMaxSitesPerBlock][8][9];
-    __shared__ int sJ[kMaxSitesPerBlock][8];  // neighbour index | flip << 31
+    __shared__ int sJ[kMaxSitesPerBlock][8];  // neighbour index
     const int n = a.nrhs;
     const size_t stride = (size_t)a.lat.Vh * n;
     constexpr int NV = EPI == EPI_XPAY_NORM ? 1 : 0;
@@ -402,9 +402,12 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(const HopArgs a) {
             cx<T> u[3][3];
             Link<P, R>::load(gbase + (size_t)((back ? 1 - a.out_parity : a.out_parity) * 4 + mu) * a.gblock, L.Vh,
                              back ? j : i, u);
+            // the time-boundary sign goes into the staged link (row 2 of a 12-real
+            // link is already rebuilt here), so the consumers never apply it
+            const T sg = flip ? T(-1) : T(1);
 #pragma unroll
-            for (int e = 0; e < 9; ++e) sU[k][d][e] = u[e / 3][e % 3];
-            sJ[k][d] = j | (flip ? (int)0x80000000u : 0);
+            for (int e = 0; e < 9; ++e) sU[k][d][e] = {sg * u[e / 3][e % 3].re, sg * u[e / 3][e % 3].im};
+            sJ[k][d] = j;
         }
         __syncthreads();
         const int k = threadIdx.y;
@@ -431,15 +434,12 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(const HopArgs a) {
             for (int e = 0; e < 12; ++e) acc[t][e] = {T(0), T(0)};
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
-            const int v = sJ[k][d];
-            const int j = v & 0x7fffffff;
-            const bool flip = v < 0;
+            const int j = sJ[k][d];
             const int mu = d >> 1;
 #pragma unroll
             for (int t = 0; t < RT; ++t) {
                 cx<T> phi[12];
-                T sc = load_for_projection<P>(a.in, stride, (size_t)j * n + r0 + t, phi);
-                if (flip) sc = -sc;
+                const T sc = load_for_projection<P>(a.in, stride, (size_t)j * n + r0 + t, phi);
                 cx<T> hh[6], uh[6];
                 // project, scale, multiply by U (forward) or U^dagger (backward), rebuild
 #define PLQ_DIR(MU)                                                                        \
@@ -450,8 +450,10 @@ __global__ void __launch_bounds__(256) hop_mrhs_kernel(const HopArgs a) {
     }
                 PLQ_DIR(0) PLQ_DIR(1) PLQ_DIR(2) PLQ_DIR(3)
 #undef PLQ_DIR
+                if constexpr (P == PLQ_F16) {  // the site norm of the FP16 storage
 #pragma unroll
-                for (int e = 0; e < 6; ++e) hh[e] = {sc * hh[e].re, sc * hh[e].im};
+                    for (int e = 0; e < 6; ++e) hh[e] = {sc * hh[e].re, sc * hh[e].im};
+                }
                 const cx<T>(*su)[9] = &sU[k][d];
 #pragma unroll
                 for (int s = 0; s < 2; ++s)

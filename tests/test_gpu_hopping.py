@@ -16,7 +16,7 @@ from paper_1405_0700_gb300 import plq  # noqa: E402
 LATTICES = [
     (2, 2, 2, 2),      # x + mu = x - mu: forward and backward hops hit the same site
     (4, 4, 4, 4),
-    (8, 8, 8, 8),      # BASELINE config 1 shape
+    (8, 8, 8, 8),      # the 8^4 small-lattice workload
     (8, 4, 4, 4),      # 4^3 x 8
     (10, 4, 6, 8),     # anisotropic: catches axis mix-ups
     (6, 2, 4, 2),      # Vh = 48: a ragged single block

@@ -353,10 +353,13 @@ __global__ void __maxnreg__(NREG) hop_kernel_capped(const HopArgs a) {
 constexpr int kMaxSitesPerBlock = 32;
 
 template <int P, int R, int EPI, bool DAG, int RT>
-__global__ void __launch_bounds__(256) hop_mrhs_kernel(const HopArgs a) {
+__global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a) {
     using T = RealOf<P>;
-    __shared__ cx<T> sU[kMaxSitesPerBlock][8][9];
-    __shared__ int sJ[kMaxSitesPerBlock][8];  // neighbour index
+    // dynamic shared memory sized for this block's sites (the rest of the SM's
+    // 256 KB stays L1 for the neighbour spinors): links, then neighbour indices
+    extern __shared__ __align__(16) unsigned char mrhs_smem[];
+    cx<T>(*sU)[8][9] = reinterpret_cast<cx<T>(*)[8][9]>(mrhs_smem);
+    int(*sJ)[8] = reinterpret_cast<int(*)[8]>(mrhs_smem + (size_t)blockDim.y * 8 * 9 * sizeof(cx<T>));
     const int n = a.nrhs;
     const size_t stride = (size_t)a.lat.Vh * n;
     constexpr int NV = EPI == EPI_XPAY_NORM ? 1 : 0;
@@ -520,23 +523,26 @@ plq_status launch_mrhs_t(const HopArgs &a, cudaStream_t s, int block) {
             break;
         }
     const int threads = tiles * spb;
-    static std::atomic<int> per_sm[257];  // occupancy per block size, filled on first use
+    using T = RealOf<P>;
+    const size_t smem = (size_t)spb * 8 * (9 * sizeof(cx<T>) + sizeof(int));
+    // occupancy per (sites per block, threads per site), filled on first use
+    static std::atomic<int> per_sm[kMaxSitesPerBlock + 1][PLQ_MAX_RHS + 1];
     auto kern = hop_mrhs_kernel<P, R, EPI, DAG, RT>;
-    if (per_sm[threads].load(std::memory_order_relaxed) == 0) {
+    if (per_sm[spb][tiles].load(std::memory_order_relaxed) == 0) {
         int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
         if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(hop_mrhs)");
-        per_sm[threads].store(nb > 0 ? nb : 1, std::memory_order_relaxed);
+        per_sm[spb][tiles].store(nb > 0 ? nb : 1, std::memory_order_relaxed);
     }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long want = ((long long)a.lat.Vh + spb - 1) / spb;
-    long long cap = (long long)per_sm[threads].load(std::memory_order_relaxed) * sms;
+    long long cap = (long long)per_sm[spb][tiles].load(std::memory_order_relaxed) * sms;
     if (EPI >= EPI_XPAY_NORM && cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
     const int grid = (int)(want < cap ? want : cap);
     if (grid <= 0) return PLQ_OK;
-    kern<<<grid, dim3(tiles, spb), 0, s>>>(a);
+    kern<<<grid, dim3(tiles, spb), smem, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "hop_mrhs_kernel launch");
     return PLQ_OK;

@@ -174,6 +174,7 @@ plq_status plq_finalize(plq_ctx *c) {
     if (c->gauge_df.ptr) cudaFree(c->gauge_df.ptr);
     for (auto &g : c->solve_graph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (c->host_graph.exec) cudaGraphExecDestroy(c->host_graph.exec);
     for (auto &t : c->nbr)
         if (t) cudaFree(t);
     if (c->partials) cudaFree(c->partials);
@@ -298,21 +299,16 @@ plq_status plq_hopping_eo(plq_ctx *c, int out_parity, void *out, const void *in,
     return launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, static_cast<cudaStream_t>(stream));
 }
 
-plq_status plq_hopping_eo_host(plq_ctx *c, int out_parity, void *out_host, const void *in_host, int prec, int nrhs,
-                               void *stream) {
-    PLQ_TRY(check_ctx(c));
-    if (!out_host || !in_host) return set_error(PLQ_ERR_ARG, "null host pointer");
-    if (out_parity != 0 && out_parity != 1) return set_error(PLQ_ERR_ARG, "out_parity must be 0 or 1");
-    if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
-    PLQ_TRY(need_gauge(c, prec));
-    PLQ_TRY(use_device(c));
+}  // extern "C"
+
+namespace {
+
+// Enqueue the host pipeline of plq_hopping_eo_host.  `origin` is the stream
+// the copies in start from and that ends ordered after the last copy out.
+plq_status enqueue_host_pipeline(plq_ctx *c, int out_parity, char *hout, const char *hin, int prec, int nrhs,
+                                 cudaStream_t origin) {
     const size_t bytes = plq_field_bytes(c, prec, nrhs);
-    PLQ_TRY(ensure_stage(c, 2 * bytes));
-    PLQ_TRY(ensure_pipeline(c));
-    cudaStream_t user = static_cast<cudaStream_t>(stream);
     char *din = static_cast<char *>(c->stage), *dout = din + bytes;
-    const char *hin = static_cast<const char *>(in_host);
-    char *hout = static_cast<char *>(out_host);
     // Pipeline over time slabs, the overlap of Sec. 2.2 applied to the host
     // link: input slabs stream in on one copy engine, the output sites whose
     // neighbours (t - 1, t, t + 1) have all arrived are computed, and finished
@@ -335,19 +331,22 @@ plq_status plq_hopping_eo_host(plq_ctx *c, int out_parity, void *out_host, const
         return e;
     };
     cudaEvent_t *ev_in = c->ev, *ev_done = c->ev + 64, *ev_start = c->ev + 128;
-    PLQ_CUDA(cudaEventRecord(ev_start[0], user));
-    PLQ_CUDA(cudaStreamWaitEvent(c->copy_in, ev_start[0], 0));
+    PLQ_CUDA(cudaEventRecord(ev_start[0], origin));
     PLQ_CUDA(cudaStreamWaitEvent(c->compute, ev_start[0], 0));
     PLQ_CUDA(cudaStreamWaitEvent(c->copy_out, ev_start[0], 0));
     // input order: the last slab first (slab 0 needs it through the periodic time direction)
     for (int q = 0; q < K; ++q) {
         const int k = (q + K - 1) % K;
-        PLQ_CUDA(copy_chunk(din, hin, k, cudaMemcpyHostToDevice, c->copy_in));
-        PLQ_CUDA(cudaEventRecord(ev_in[k], c->copy_in));
+        PLQ_CUDA(copy_chunk(din, hin, k, cudaMemcpyHostToDevice, origin));
+        PLQ_CUDA(cudaEventRecord(ev_in[k], origin));
     }
     for (int k = 0; k < K; ++k) {
-        PLQ_CUDA(cudaStreamWaitEvent(c->compute, ev_in[(k + K - 1) % K], 0));
-        PLQ_CUDA(cudaStreamWaitEvent(c->compute, ev_in[k], 0));
+        // slabs k - 1 and k arrived before slab k + 1 (copy order), except
+        // at the start, where K - 1, 0 and 1 are needed
+        if (k == 0) {
+            PLQ_CUDA(cudaStreamWaitEvent(c->compute, ev_in[K - 1], 0));
+            PLQ_CUDA(cudaStreamWaitEvent(c->compute, ev_in[0], 0));
+        }
         PLQ_CUDA(cudaStreamWaitEvent(c->compute, ev_in[(k + 1) % K], 0));
         HopArgs a = hop_args(c, prec, out_parity, dout, din, nrhs);
         a.site_begin = chunk_t0(k) * slab;
@@ -359,7 +358,74 @@ plq_status plq_hopping_eo_host(plq_ctx *c, int out_parity, void *out_host, const
         PLQ_CUDA(copy_chunk(hout, dout, k, cudaMemcpyDeviceToHost, c->copy_out));
     }
     PLQ_CUDA(cudaEventRecord(ev_start[1], c->copy_out));
-    PLQ_CUDA(cudaStreamWaitEvent(user, ev_start[1], 0));
+    PLQ_CUDA(cudaStreamWaitEvent(origin, ev_start[1], 0));
+    return PLQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+plq_status plq_hopping_eo_host(plq_ctx *c, int out_parity, void *out_host, const void *in_host, int prec, int nrhs,
+                               void *stream) {
+    PLQ_TRY(check_ctx(c));
+    if (!out_host || !in_host) return set_error(PLQ_ERR_ARG, "null host pointer");
+    if (out_parity != 0 && out_parity != 1) return set_error(PLQ_ERR_ARG, "out_parity must be 0 or 1");
+    if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
+    PLQ_TRY(need_gauge(c, prec));
+    PLQ_TRY(use_device(c));
+    const size_t bytes = plq_field_bytes(c, prec, nrhs);
+    PLQ_TRY(ensure_stage(c, 2 * bytes));
+    PLQ_TRY(ensure_pipeline(c));
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    const char *hin = static_cast<const char *>(in_host);
+    char *hout = static_cast<char *>(out_host);
+    // The ~150 copies, launches and event operations of the pipeline are
+    // captured once into a CUDA graph and replayed while the buffers and the
+    // launch configuration stay the same (pageable host memory, which graphs
+    // cannot copy from asynchronously, takes the direct path).
+    cudaPointerAttributes pa{}, pb{};
+    const bool pinned = cudaPointerGetAttributes(&pa, hin) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+                        cudaPointerGetAttributes(&pb, hout) == cudaSuccess && pb.type == cudaMemoryTypeHost;
+    cudaGetLastError();  // a pageable pointer may leave an error from the attribute query
+    // (the captured launches hold the gauge copy's address: a re-upload in another
+    // link format reallocates it)
+    unsigned long long key[8] = {reinterpret_cast<uintptr_t>(hin),
+                                 reinterpret_cast<uintptr_t>(hout),
+                                 (unsigned long long)prec | ((unsigned long long)nrhs << 8) |
+                                     ((unsigned long long)out_parity << 16) |
+                                     ((unsigned long long)c->gauge[prec].reals << 24),
+                                 reinterpret_cast<uintptr_t>(c->stage),
+                                 (unsigned long long)c->tune_version,
+                                 reinterpret_cast<uintptr_t>(c->gauge[prec].ptr),
+                                 (unsigned long long)c->gauge[prec].block,
+                                 1ull};
+    Ctx::HostGraph &hg = c->host_graph;
+    if (pinned && !(hg.exec && std::memcmp(hg.key, key, sizeof(key)) == 0)) {
+        if (hg.exec) {
+            cudaGraphExecDestroy(hg.exec);
+            hg.exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        PLQ_CUDA(cudaStreamBeginCapture(c->copy_in, cudaStreamCaptureModeThreadLocal));
+        plq_status st = enqueue_host_pipeline(c, out_parity, hout, hin, prec, nrhs, c->copy_in);
+        cudaError_t e = cudaStreamEndCapture(c->copy_in, &graph);
+        if (st == PLQ_OK && e == cudaSuccess) e = cudaGraphInstantiate(&hg.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (st != PLQ_OK) return st;
+        if (e != cudaSuccess) {
+            hg.exec = nullptr;
+            return cuda_error(e, "host pipeline graph");
+        }
+        std::memcpy(hg.key, key, sizeof(key));
+    }
+    cudaEvent_t *ev_start = c->ev + 128;
+    PLQ_CUDA(cudaEventRecord(ev_start[2], user));
+    PLQ_CUDA(cudaStreamWaitEvent(c->copy_in, ev_start[2], 0));
+    if (pinned) PLQ_CUDA(cudaGraphLaunch(hg.exec, c->copy_in));
+    else PLQ_TRY(enqueue_host_pipeline(c, out_parity, hout, hin, prec, nrhs, c->copy_in));
+    PLQ_CUDA(cudaEventRecord(ev_start[3], c->copy_in));
+    PLQ_CUDA(cudaStreamWaitEvent(user, ev_start[3], 0));
     PLQ_CUDA(cudaStreamSynchronize(user));
     return PLQ_OK;
 }

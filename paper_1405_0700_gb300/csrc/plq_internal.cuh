@@ -139,12 +139,18 @@ struct Ctx {
     // Instantiated inner-iteration graph of the last CG / BiCGstab solve, reused
     // by the next reliable-update cycle and the next solve with the same key
     // (method, precisions, sizes, kappa, mu, batch length, workspace address,
-    // launch configuration version).
+    // launch configuration version, inner gauge copy address and format).
     struct SolveGraph {
         cudaGraphExec_t exec = nullptr;
         unsigned long long key[10] = {};
     } solve_graph[2];
     unsigned tune_version = 0;  // bumped whenever a launch configuration changes
+    // Instantiated pipeline of plq_hopping_eo_host for the last (host buffers,
+    // precision, nrhs, parity, staging area, launch version) it ran with.
+    struct HostGraph {
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long key[8] = {};
+    } host_graph;
 };
 
 plq_status ensure_work(Ctx *c, size_t bytes);

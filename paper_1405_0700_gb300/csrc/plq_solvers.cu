@@ -166,6 +166,9 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
         gkey[6] = (unsigned long long)reinterpret_cast<uintptr_t>(c->work);
         gkey[7] = (unsigned long long)c->tune_version;
         gkey[8] = 1;  // marks a valid key
+        // the captured launches hold the inner gauge copy's address and format
+        gkey[9] = (unsigned long long)reinterpret_cast<uintptr_t>(c->gauge[S.P].ptr) ^
+                  ((unsigned long long)c->gauge[S.P].reals << 56);
     }
 
     // internal stream ordered after the caller's stream

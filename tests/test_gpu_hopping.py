@@ -133,20 +133,32 @@ def test_multi_rhs_tiles(tile, zc, sm, prec, reals):
         assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
 
 
-def test_host_entry_point_matches_device():
-    dims = (8, 4, 4, 4)
-    U, phi = S.gauge_and_spinor(dims, 0.3, 7)
+@pytest.mark.parametrize("prec,reals,nrhs", [(F32, 18, 1), (F16, 12, 1), (F32, 12, 3), (F64, 18, 2)])
+def test_host_entry_point_matches_device(prec, reals, nrhs):
+    """plq_hopping_eo_host (time-slab pipeline; captured as a graph for pinned buffers
+    and replayed while they stay the same) equals plq_hopping_eo bit for bit, for
+    pinned and pageable host buffers, repeated calls and a change of buffers."""
+    dims = (16, 4, 4, 6)
+    U = S.gauge_field(dims, 0.3, 7)
+    phis = np.stack([S.gaussian_spinor(dims, 70 + r) for r in range(nrhs)])
     with Context(dims) as ctx:
-        ctx.gauge_upload(U, 18, F32)
-        full = ctx.to_device(phi, F32)
-        e_in, o_in = ctx.halves(full, F32)
-        dev_out = ctx.empty_half(F32)
-        ctx.hopping_eo(0, dev_out, o_in, F32)
-        host_in = o_in.cpu().pin_memory()
-        host_out = torch.empty_like(host_in).pin_memory()
-        ctx.hopping_eo_host(0, host_out, host_in, F32)
-        torch.cuda.synchronize()
-        assert torch.equal(host_out, dev_out.cpu())
+        ctx.gauge_upload(U, reals, prec)
+        full = ctx.to_device(phis if nrhs > 1 else phis[0], prec, nrhs)
+        e_in, o_in = ctx.halves(full, prec, nrhs)
+        dev_out = ctx.empty_half(prec, nrhs)
+        for parity, src in ((0, o_in), (1, e_in)):
+            ctx.hopping_eo(parity, dev_out, src, prec, nrhs)
+            expect = dev_out.cpu()
+            for pinned in (True, False):
+                host_in = src.cpu()
+                host_out = torch.zeros_like(host_in)
+                if pinned:
+                    host_in, host_out = host_in.pin_memory(), host_out.pin_memory()
+                for _ in range(2):  # the second call replays the captured pipeline
+                    host_out.zero_()
+                    ctx.hopping_eo_host(parity, host_out, host_in, prec, nrhs)
+                    torch.cuda.synchronize()
+                    assert torch.equal(host_out, expect), (parity, pinned)
 
 
 def test_errors_are_reported_not_faulted():
@@ -229,3 +241,22 @@ def test_autotune_and_cache(tmp_path):
         r2 = ctx.autotune(F32, 1, cache_path=cache)
         assert r2["from_cache"] == 1 and r2["block"] == r["block"] and r2["index_mode"] == r["index_mode"]
     assert open(cache).read().count("\n") == 1
+
+
+def test_host_entry_point_follows_gauge_format_change():
+    dims = (8, 4, 4, 4)
+    U, phi = S.gauge_and_spinor(dims, 0.3, 12)
+    with Context(dims) as ctx:
+        host_in = host_out = None
+        for reals in (18, 12, 18):
+            ctx.gauge_upload(U, reals, F32)
+            full = ctx.to_device(phi, F32)
+            e_in, o_in = ctx.halves(full, F32)
+            dev_out = ctx.empty_half(F32)
+            ctx.hopping_eo(0, dev_out, o_in, F32)
+            if host_in is None:
+                host_in = o_in.cpu().pin_memory()
+                host_out = torch.empty_like(host_in).pin_memory()
+            ctx.hopping_eo_host(0, host_out, host_in, F32)
+            torch.cuda.synchronize()
+            assert torch.equal(host_out, dev_out.cpu()), reals

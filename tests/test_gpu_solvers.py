@@ -290,3 +290,25 @@ def test_batched_zero_source_and_maxit():
         P.cg_solve_batched([ctx], [x], [bd], [0.12], inner_prec=F32, maxit=3)
     assert e.value.status == plq.PLQ_ERR_NOT_CONVERGED
     ctx.close()
+
+
+def test_solver_graph_follows_gauge_and_launch_changes():
+    """The instantiated inner-iteration graph is reused between solves; a new gauge
+    field, another link format (a reallocated copy), another kappa or another launch
+    configuration must each give the correct solution of the new system."""
+    dims = (8, 4, 4, 8)
+    U1, b = S.gauge_and_spinor(dims, 0.3, 81)
+    U2 = S.gauge_field(dims, 0.3, 82)
+    with Context(dims) as ctx:
+        bd = ctx.to_device(b, F64)
+        x = ctx.empty_full(F64)
+        steps = [(U1, 12, 0.12, None), (U1, 12, 0.12, None), (U2, 12, 0.12, None), (U2, 18, 0.12, None),
+                 (U2, 18, 0.115, None), (U2, 18, 0.115, 64)]
+        for U, reals, kappa, block in steps:
+            ctx.gauge_upload(U, 18, F64)
+            ctx.gauge_upload(U, reals, F32)
+            if block:
+                ctx.set_launch(F32, 1, block, 0, 1, 0, 0)
+            ctx.cg_solve(x, bd, kappa, inner_prec=F32)
+            res = oracle_residual(U, b, ctx.to_host(x, F64), kappa)
+            assert res <= 1e-10, (reals, kappa, block, res)

@@ -135,6 +135,9 @@ typedef struct {
                           PLQ_DF64 gauge copy).  The residual of the returned x is always
                           computed in FP64.  Used by plq_cg_solve(_multi) and
                           plq_bicgstab_solve(_multi); other solvers ignore it.               */
+    double wait_limit_s; /* plq_cg_solve_batched: longest a block of the persistent kernel
+                            may wait at a grid barrier before the solve gives up with
+                            PLQ_ERR_TIMEOUT (0: about 5 s)                                   */
 } plq_solver_params;
 
 /* Per-solve report. */
@@ -309,8 +312,9 @@ typedef struct {
  * as its own state machine; all systems advance in lockstep phases separated
  * by grid-wide barriers, and the sites of every still-active system form one
  * shared work range, so converged systems retire and their blocks move to the
- * others.  Barriers wait with a time limit (about 5 s) and report
- * PLQ_ERR_TIMEOUT instead of hanging.  Each context needs an 18-real FP64
+ * others.  Barriers wait with a time limit (params->wait_limit_s, default
+ * about 5 s) and report PLQ_ERR_TIMEOUT instead of hanging: every block
+ * leaves the kernel and the context stays usable.  Each context needs an 18-real FP64
  * gauge copy and a copy of the inner precision (the same link format for all
  * systems; FP16 inner solves use 12-real links).  x[k], b[k]: packed full
  * FP64 fields of context k.  infos (n entries) and binfo may be NULL.  After

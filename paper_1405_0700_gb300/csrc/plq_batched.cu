@@ -714,7 +714,13 @@ extern "C" plq_status plq_cg_solve_batched(plq_ctx **ctxs, int n, void **x, cons
         a.bar_count = reinterpret_cast<unsigned *>(words);
         a.bar_gen = reinterpret_cast<unsigned *>(words + 16);
         a.status = reinterpret_cast<int *>(words + 32);
-        a.spin_limit = 10LL * 1000 * 1000 * 1000;  // ~5 s of clock cycles at 2 GHz
+        {
+            int khz = 0;  // SM clock in kHz (clock64 counts SM cycles)
+            cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device);
+            const double lim = (params && params->wait_limit_s > 0) ? params->wait_limit_s : 5.0;
+            const double cyc = lim * (khz > 0 ? khz : 2000000) * 1e3;
+            a.spin_limit = cyc < 1.0 ? 1LL : cyc > 1e15 ? (long long)1e15 : (long long)cyc;
+        }
         a.max_phases = 16LL * (maxit + 64) + 4096;
         auto t0 = std::chrono::steady_clock::now();
         if (inner == PLQ_F64) stt = launch_batched<PLQ_F64, 18>(a, s, &grid, &block, &captured);

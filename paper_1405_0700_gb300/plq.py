@@ -46,6 +46,7 @@ class SolverParams(ctypes.Structure):
         ("check_every", ctypes.c_int),
         ("mu", ctypes.c_double),
         ("residual_prec", ctypes.c_int),
+        ("wait_limit_s", ctypes.c_double),
     ]
 
 
@@ -383,14 +384,15 @@ class Context:
 
 
 def cg_solve_batched(ctxs, xs, bs, kappas, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0, use_x0=False,
-                     stream=None, raise_on_error=True):
-    """One persistent launch solving len(ctxs) independent systems (see plq_cg_solve_batched)."""
+                     stream=None, raise_on_error=True, wait_limit_s=0.0):
+    """One persistent launch solving len(ctxs) independent systems (see plq_cg_solve_batched).
+    wait_limit_s bounds each grid-barrier wait (0: the library default, about 5 s)."""
     n = len(ctxs)
     H = (_vp * n)(*[c.handle.value for c in ctxs])
     X = (_vp * n)(*[_ptr(x) for x in xs])
     B = (_vp * n)(*[_ptr(b) for b in bs])
     K = (ctypes.c_double * n)(*[float(k) for k in kappas])
-    p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), 16, 0.0, F64)
+    p = SolverParams(tol, maxit, prec_of(inner_prec), delta, int(use_x0), 16, 0.0, F64, float(wait_limit_s))
     infos = (SolveInfo * n)()
     bi = BatchInfo()
     st = lib().plq_cg_solve_batched(H, n, X, B, K, ctypes.byref(p), infos, ctypes.byref(bi), _stream(stream))

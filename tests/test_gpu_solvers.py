@@ -292,6 +292,30 @@ def test_batched_zero_source_and_maxit():
     ctx.close()
 
 
+def test_batched_barrier_wait_limit_reports_timeout():
+    """A grid-barrier wait limit of one clock cycle: the first block to wait at a
+    barrier gives up, every block leaves the persistent kernel (the others see the
+    status word at their next barrier), the call returns PLQ_ERR_TIMEOUT, and the
+    same contexts then solve normally."""
+    from paper_1405_0700_gb300 import plq as P
+
+    dims = (8, 4, 4, 8)
+    U, b = S.gauge_and_spinor(dims, 0.3, 63)
+    ctx = Context(dims)
+    ctx.gauge_upload(U, 18, F64)
+    ctx.gauge_upload(U, 12, F32)
+    bd = ctx.to_device(b, F64)
+    x = ctx.empty_full(F64)
+    with pytest.raises(PLQError) as e:
+        P.cg_solve_batched([ctx], [x], [bd], [0.12], inner_prec=F32, wait_limit_s=1e-12)
+    assert e.value.status == plq.PLQ_ERR_TIMEOUT
+    torch.cuda.synchronize()
+    infos, binfo = P.cg_solve_batched([ctx], [x], [bd], [0.12], inner_prec=F32)
+    assert binfo["launches"] == 1
+    assert oracle_residual(U, b, ctx.to_host(x, F64), 0.12) <= 1e-10
+    ctx.close()
+
+
 def test_solver_graph_follows_gauge_and_launch_changes():
     """The instantiated inner-iteration graph is reused between solves; a new gauge
     field, another link format (a reallocated copy), another kappa or another launch

@@ -358,7 +358,9 @@ typedef struct {
     int index_mode;       /* 0: neighbours from coordinates; 1: precomputed neighbour table */
     int rhs_tile;         /* right-hand sides per thread (each loaded link serves all)     */
     int z_chunk;          /* site order: 0 = time slowest; z > 0 = z-chunks of z planes    */
-    int smem_links;       /* nrhs > 1: links of a block of sites staged in shared memory  */
+    int smem_links;       /* nrhs > 1: 0 none; 1 links of a block of sites staged in shared
+                             memory; 2 / 3 the same plus the neighbour spinors of the next
+                             1 / 2 directions copied ahead into per-thread shared slots   */
     double us_per_launch; /* measured time of one half-lattice application                 */
     int from_cache;       /* 1 if the choice came from the cache file                      */
     int candidates;       /* configurations timed                                          */
@@ -372,7 +374,9 @@ typedef struct {
  * and FP16 storage) with 2 or 4 right-hand sides per thread (register tiles
  * that reuse each loaded link, Sec. 2.3's one-matrix-two-vectors idea
  * widened), with the links of a block of sites staged once in shared memory
- * (nrhs > 1), and with the sites walked in z-chunks of 8 or 4 planes (time
+ * (nrhs > 1; with or without the neighbour spinors of the next directions
+ * copied ahead asynchronously, the GPU counterpart of the paper's software
+ * prefetch, Sec. 2.2), and with the sites walked in z-chunks of 8 or 4 planes (time
  * inside a chunk, which keeps the data reused through the time direction
  * within L2 for large multi-RHS fields), and keeps the fastest in
  * the context for every later operator and solver call of that precision.
@@ -386,7 +390,8 @@ PLQ_API plq_status plq_autotune(plq_ctx *ctx, int prec, int nrhs, const char *ca
 /* Set the hopping launch of (prec, nrhs) by hand: block = threads per block
  * (0 = library default, else a multiple of 32 up to 256), index_mode 0 or 1,
  * rhs_tile 1, 2 or 4 (dividing nrhs), z_chunk 0 or a divisor of Lz and
- * smem_links 0/1 (nrhs > 1, FP32/FP16; with it rhs_tile 1 or 2), as above. */
+ * smem_links 0..3 (nrhs > 1, FP32/FP16; with 1, rhs_tile 1 or 2; with 2 or 3,
+ * rhs_tile 1), as above. */
 PLQ_API plq_status plq_set_launch(plq_ctx *ctx, int prec, int nrhs, int block, int index_mode, int rhs_tile,
                                   int z_chunk, int smem_links);
 

@@ -352,14 +352,60 @@ __global__ void __maxnreg__(NREG) hop_kernel_capped(const HopArgs a) {
 // plain multi-RHS kernel.
 constexpr int kMaxSitesPerBlock = 32;
 
-template <int P, int R, int EPI, bool DAG, int RT>
+// Asynchronous global -> shared copies (cp.async; completion is tracked per
+// thread in commit groups, so a thread that copies into and reads from its own
+// slots needs no block barrier).  The 16-byte form bypasses L1.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most `pending` of this thread's groups are still in flight
+__device__ __forceinline__ void cp_async_wait(int pending) {
+    if (pending <= 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    else if (pending == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    else asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+}
+
+// 16-byte planes of one spinor element in storage format P: 6 (FP32: two
+// complex numbers each), 3 (FP16: four each, plus a float site norm)
+template <int P>
+constexpr int spinor_planes() {
+    return P == PLQ_F16 ? 3 : 6;
+}
+
+// Shared memory of the multi-RHS kernel for `sites` sites and `threads`
+// threads: links and neighbour indices, then NB per-thread slots of one
+// neighbour spinor (16-byte planes, then the FP16 norms).
+template <int P, int NB>
+__host__ __device__ constexpr size_t mrhs_smem_bytes(int sites, int threads) {
+    return (((size_t)sites * 8 * (9 * sizeof(cx<RealOf<P>>) + sizeof(int)) + 15) & ~(size_t)15) +
+           (size_t)NB * threads * (16 * spinor_planes<P>() + (P == PLQ_F16 ? sizeof(float) : 0));
+}
+
+// NB = 0: each thread loads its neighbour spinors straight into registers.
+// NB = 2 or 3 (one right-hand side per thread): the spinors of the next NB - 1
+// directions are already on their way into the thread's shared-memory slots
+// while it computes the current direction.  The loads of this kernel mostly
+// miss L1 and wait on L2; with 80 registers a thread can hold only one
+// direction's spinor, so the copies into shared memory are what lets a thread
+// keep more than one direction's loads in flight.
+template <int P, int R, int EPI, bool DAG, int RT, int NB>
 __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a) {
+    static_assert(NB == 0 || (RT == 1 && NB >= 2 && NB <= 3), "spinor slots need one RHS per thread");
     using T = RealOf<P>;
+    constexpr int NP = spinor_planes<P>();
     // dynamic shared memory sized for this block's sites (the rest of the SM's
     // 256 KB stays L1 for the neighbour spinors): links, then neighbour indices
     extern __shared__ __align__(16) unsigned char mrhs_smem[];
     cx<T>(*sU)[8][9] = reinterpret_cast<cx<T>(*)[8][9]>(mrhs_smem);
     int(*sJ)[8] = reinterpret_cast<int(*)[8]>(mrhs_smem + (size_t)blockDim.y * 8 * 9 * sizeof(cx<T>));
+    uint4 *sP = reinterpret_cast<uint4 *>(mrhs_smem + mrhs_smem_bytes<P, 0>(blockDim.y, 0));
+    float *sN = reinterpret_cast<float *>(sP + (size_t)NB * NP * blockDim.x * blockDim.y);
     const int n = a.nrhs;
     const size_t stride = (size_t)a.lat.Vh * n;
     constexpr int NV = EPI == EPI_XPAY_NORM ? 1 : 0;
@@ -430,6 +476,21 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
 #pragma unroll
         for (int t = 0; t < RT; ++t) all_frozen = all_frozen && a.st[r0 + t].stop;
         if (all_frozen) continue;
+        // copy the neighbour spinor of direction d into slot b of this thread
+        auto issue = [&](int d, int b) {
+            const size_t e = (size_t)sJ[k][d] * n + r0;
+            const uint4 *src = static_cast<const uint4 *>(a.in) + e;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) cp_async16(&sP[(size_t)(b * NP + q) * nthr + tid], src + q * stride);
+            if constexpr (P == PLQ_F16)
+                cp_async4(&sN[b * nthr + tid],
+                          reinterpret_cast<const float *>(static_cast<const uint4 *>(a.in) + NP * stride) + e);
+            cp_async_commit();
+        };
+        if constexpr (NB > 0) {
+#pragma unroll
+            for (int d = 0; d < NB - 1; ++d) issue(d, d);
+        }
         cx<T> acc[RT][12];
 #pragma unroll
         for (int t = 0; t < RT; ++t)
@@ -439,10 +500,42 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
         for (int d = 0; d < 8; ++d) {
             const int j = sJ[k][d];
             const int mu = d >> 1;
+            if constexpr (NB > 0) {
+                (void)j;
+                // slot (d + NB - 1) % NB was read in the previous direction, whose
+                // arithmetic has consumed the values
+                if (d + NB - 1 < 8) issue(d + NB - 1, (d + NB - 1) % NB);
+                cp_async_wait(d + NB - 1 < 8 ? NB - 1 : 7 - d);
+            }
 #pragma unroll
             for (int t = 0; t < RT; ++t) {
                 cx<T> phi[12];
-                const T sc = load_for_projection<P>(a.in, stride, (size_t)j * n + r0 + t, phi);
+                T sc;
+                if constexpr (NB > 0) {
+                    const int b = d % NB;
+                    if constexpr (P == PLQ_F16) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            const uint4 v = sP[(size_t)(b * NP + q) * nthr + tid];
+                            const float2 x0 = h2f(v.x), x1 = h2f(v.y), x2 = h2f(v.z), x3 = h2f(v.w);
+                            phi[4 * q + 0] = {x0.x, x0.y};
+                            phi[4 * q + 1] = {x1.x, x1.y};
+                            phi[4 * q + 2] = {x2.x, x2.y};
+                            phi[4 * q + 3] = {x3.x, x3.y};
+                        }
+                        sc = sN[b * nthr + tid];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) {
+                            const float4 v = reinterpret_cast<const float4 *>(sP)[(size_t)(b * NP + q) * nthr + tid];
+                            phi[2 * q] = {v.x, v.y};
+                            phi[2 * q + 1] = {v.z, v.w};
+                        }
+                        sc = T(1);
+                    }
+                } else {
+                    sc = load_for_projection<P>(a.in, stride, (size_t)j * n + r0 + t, phi);
+                }
                 cx<T> hh[6], uh[6];
                 // project, scale, multiply by U (forward) or U^dagger (backward), rebuild
 #define PLQ_DIR(MU)                                                                        \
@@ -509,7 +602,7 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
     if constexpr (NV > 0) grid_reduce(a.red, racc);
 }
 
-template <int P, int R, int EPI, bool DAG, int RT>
+template <int P, int R, int EPI, bool DAG, int RT, int NB>
 plq_status launch_mrhs_t(const HopArgs &a, cudaStream_t s, int block) {
     if (a.block > 0) block = a.block;
     if (block <= 0 || block > 256) block = 128;
@@ -523,14 +616,16 @@ plq_status launch_mrhs_t(const HopArgs &a, cudaStream_t s, int block) {
             break;
         }
     const int threads = tiles * spb;
-    using T = RealOf<P>;
-    const size_t smem = (size_t)spb * 8 * (9 * sizeof(cx<T>) + sizeof(int));
+    const size_t smem = mrhs_smem_bytes<P, NB>(spb, threads);
     // occupancy per (sites per block, threads per site), filled on first use
     static std::atomic<int> per_sm[kMaxSitesPerBlock + 1][PLQ_MAX_RHS + 1];
-    auto kern = hop_mrhs_kernel<P, R, EPI, DAG, RT>;
+    auto kern = hop_mrhs_kernel<P, R, EPI, DAG, RT, NB>;
     if (per_sm[spb][tiles].load(std::memory_order_relaxed) == 0) {
         int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
+        cudaError_t e = cudaSuccess;
+        if (smem > 48 * 1024)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
         if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(hop_mrhs)");
         per_sm[spb][tiles].store(nb > 0 ? nb : 1, std::memory_order_relaxed);
     }
@@ -548,18 +643,18 @@ plq_status launch_mrhs_t(const HopArgs &a, cudaStream_t s, int block) {
     return PLQ_OK;
 }
 
-template <int P, int R, int RT>
+template <int P, int R, int RT, int NB>
 plq_status dispatch_mrhs(const HopArgs &a, int epi, cudaStream_t s, int block) {
     switch (epi) {
     case EPI_PLAIN:
-        return a.dagger ? launch_mrhs_t<P, R, EPI_PLAIN, true, RT>(a, s, block)
-                        : launch_mrhs_t<P, R, EPI_PLAIN, false, RT>(a, s, block);
+        return a.dagger ? launch_mrhs_t<P, R, EPI_PLAIN, true, RT, NB>(a, s, block)
+                        : launch_mrhs_t<P, R, EPI_PLAIN, false, RT, NB>(a, s, block);
     case EPI_XPAY:
-        return a.dagger ? launch_mrhs_t<P, R, EPI_XPAY, true, RT>(a, s, block)
-                        : launch_mrhs_t<P, R, EPI_XPAY, false, RT>(a, s, block);
+        return a.dagger ? launch_mrhs_t<P, R, EPI_XPAY, true, RT, NB>(a, s, block)
+                        : launch_mrhs_t<P, R, EPI_XPAY, false, RT, NB>(a, s, block);
     default:
-        return a.dagger ? launch_mrhs_t<P, R, EPI_XPAY_NORM, true, RT>(a, s, block)
-                        : launch_mrhs_t<P, R, EPI_XPAY_NORM, false, RT>(a, s, block);
+        return a.dagger ? launch_mrhs_t<P, R, EPI_XPAY_NORM, true, RT, NB>(a, s, block)
+                        : launch_mrhs_t<P, R, EPI_XPAY_NORM, false, RT, NB>(a, s, block);
     }
 }
 
@@ -629,8 +724,10 @@ plq_status dispatch_hop(const HopArgs &a, int epi, cudaStream_t s, int block) {
     // neighbour-table variants for the plain and xpay epilogues.
     if constexpr (P != PLQ_F64) {
         if (a.smem_links && a.nrhs > 1 && a.site_begin == 0 && a.site_end < 0 && epi <= EPI_XPAY_NORM) {
-            if (a.rhs_tile == 2 && a.nrhs % 2 == 0) return dispatch_mrhs<P, R, 2>(a, epi, s, block);
-            return dispatch_mrhs<P, R, 1>(a, epi, s, block);
+            if (a.rhs_tile == 2 && a.nrhs % 2 == 0) return dispatch_mrhs<P, R, 2, 0>(a, epi, s, block);
+            if (a.smem_links == 2) return dispatch_mrhs<P, R, 1, 2>(a, epi, s, block);
+            if (a.smem_links == 3) return dispatch_mrhs<P, R, 1, 3>(a, epi, s, block);
+            return dispatch_mrhs<P, R, 1, 0>(a, epi, s, block);
         }
         if (a.rhs_tile > 1 && a.nrhs % a.rhs_tile == 0 && epi <= EPI_XPAY_NORM) {
             if (a.rhs_tile == 2) return dispatch_tiled<P, R, 2>(a, epi, s, block);

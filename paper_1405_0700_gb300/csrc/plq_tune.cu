@@ -51,7 +51,8 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
         char k[600];
         int block = 0, mode = 0, tile = 1, zc = 0, sm = 0;
         float us = 0;
-        if (sscanf(line, "%599s %d %d %d %d %d %f", k, &block, &mode, &tile, &zc, &sm, &us) == 7 && key == k) {
+        if (sscanf(line, "%599s %d %d %d %d %d %f", k, &block, &mode, &tile, &zc, &sm, &us) == 7 && key == k &&
+            sm >= 0 && sm <= 3) {
             e->block = block;
             e->index_mode = mode;
             e->rhs_tile = tile;
@@ -150,7 +151,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
     struct Cand {
         int mode, tile, zc, smem;
     };
-    Cand cands[24];
+    Cand cands[32];
     int nc = 0;
     const int Lz = c->lat.L[3];
     int zcs[3] = {0, 0, 0}, nz = 1;
@@ -163,6 +164,10 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
         if (prec != PLQ_F64 && nrhs % 2 == 0) cands[nc++] = {0, 2, z, 0};
         if (prec != PLQ_F64 && nrhs % 4 == 0) cands[nc++] = {0, 4, z, 0};
         if (prec != PLQ_F64 && nrhs > 1) cands[nc++] = {0, 1, z, 1};
+        // neighbour spinors copied ahead into shared memory: wins for FP16 storage
+        // on large lattices (site order chunks did not add to it)
+        if (prec != PLQ_F64 && nrhs > 1 && z == 0) cands[nc++] = {0, 1, z, 2};
+        if (prec != PLQ_F64 && nrhs > 1 && z == 0) cands[nc++] = {0, 1, z, 3};
         if (prec != PLQ_F64 && nrhs > 1 && nrhs % 2 == 0) cands[nc++] = {0, 2, z, 1};
     }
     for (int ci = 0; ci < nc && st == PLQ_OK; ++ci) {
@@ -239,13 +244,15 @@ extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, 
     if (nrhs % rhs_tile) return set_error(PLQ_ERR_ARG, "rhs_tile must divide nrhs");
     if (z_chunk < 0 || (z_chunk > 0 && c->lat.L[3] % z_chunk))
         return set_error(PLQ_ERR_ARG, "z_chunk must be 0 or divide Lz");
+    if (smem_links < 0 || smem_links > 3) return set_error(PLQ_ERR_ARG, "smem_links must be 0, 1, 2 or 3");
+    if (smem_links >= 2 && rhs_tile != 1) return set_error(PLQ_ERR_ARG, "smem_links 2 and 3 need rhs_tile 1");
     PLQ_CUDA(cudaSetDevice(c->device));
     if (index_mode == 1) PLQ_TRY(ensure_nbr_tables(c));
     c->tune[prec][nrhs].block = block;
     c->tune[prec][nrhs].index_mode = index_mode;
     c->tune[prec][nrhs].rhs_tile = rhs_tile;
     c->tune[prec][nrhs].zc = z_chunk;
-    c->tune[prec][nrhs].smem_links = smem_links ? 1 : 0;
+    c->tune[prec][nrhs].smem_links = smem_links;
     ++c->tune_version;
     return PLQ_OK;
 }

@@ -116,7 +116,8 @@ def test_multi_rhs(nrhs, prec, reals):
         assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
 
 
-@pytest.mark.parametrize("tile,zc,sm", [(2, 0, 0), (4, 0, 0), (1, 2, 0), (2, 4, 0), (1, 0, 1), (2, 4, 1)])
+@pytest.mark.parametrize("tile,zc,sm", [(2, 0, 0), (4, 0, 0), (1, 2, 0), (2, 4, 0), (1, 0, 1), (2, 4, 1),
+                                        (1, 0, 2), (1, 4, 3)])
 @pytest.mark.parametrize("prec,reals", [(F32, 18), (F32, 12), (F16, 12), (F16, 18)])
 def test_multi_rhs_tiles(tile, zc, sm, prec, reals):
     # each thread applies every link it loads to `tile` right-hand sides; zc walks the
@@ -131,6 +132,33 @@ def test_multi_rhs_tiles(tile, zc, sm, prec, reals):
         got = gpu_hopping_full(ctx, phis, prec, nrhs).reshape(phis.shape)
     for r in range(nrhs):
         assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
+
+
+@pytest.mark.parametrize("sm", [1, 2, 3])
+@pytest.mark.parametrize("prec,reals", [(F32, 18), (F16, 12)])
+@pytest.mark.parametrize("nrhs,block", [(5, 96), (2, 256), (3, 64)])
+def test_multi_rhs_shared_staging_ragged(sm, prec, reals, nrhs, block):
+    """Shared-memory link staging, with and without the neighbour spinors copied ahead
+    (1 or 2 directions), for right-hand-side counts whose sites per block do not divide
+    the half volume (a ragged last block) and blocks that are not whole warps."""
+    dims = (6, 4, 2, 6)
+    U = S.gauge_field(dims, 0.3, 17)
+    phis = np.stack([S.gaussian_spinor(dims, 300 + r) for r in range(nrhs)])
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, reals, prec)
+        ctx.set_launch(prec, nrhs, block, 0, 1, 0, sm)
+        got = gpu_hopping_full(ctx, phis, prec, nrhs).reshape(phis.shape)
+    for r in range(nrhs):
+        assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
+
+
+def test_set_launch_rejects_bad_staging():
+    dims = (4, 4, 2, 4)
+    with Context(dims) as ctx:
+        for sm, tile in ((4, 1), (-1, 1), (2, 2), (3, 4)):
+            with pytest.raises(PLQError) as e:
+                ctx.set_launch(F32, 4, 64, 0, tile, 0, sm)
+            assert e.value.status == plq.PLQ_ERR_ARG
 
 
 @pytest.mark.parametrize("prec,reals,nrhs", [(F32, 18, 1), (F16, 12, 1), (F32, 12, 3), (F64, 18, 2)])

@@ -158,7 +158,7 @@ def test_multi_rhs_point_sources(method, inner):
         assert abs(infos[r].true_rel_residual - res) < 1e-11
 
 
-@pytest.mark.parametrize("tile,sm", [(2, 0), (4, 0), (1, 1), (2, 1)])
+@pytest.mark.parametrize("tile,sm", [(2, 0), (4, 0), (1, 1), (2, 1), (1, 2), (1, 3)])
 def test_multi_rhs_cg_with_rhs_tiles(tile, sm):
     dims = (8, 4, 4, 8)
     kappa = 0.12

@@ -492,10 +492,11 @@ def operator_only(args, torch, local_rank):
         ctx.gauge_upload(U, args.links, prec)
         tuned = ctx.autotune(prec, n) if args.tune and args.prec != "df64" else None
         if args.launch and args.prec != "df64":  # the float-float kernel has one fixed launch shape
-            vals = [int(v) for v in args.launch.split(",")] + [0]
-            blk, mode, tile, zc, sm = vals[:5]
-            ctx.set_launch(prec, n, blk, mode, tile, zc, sm)
-            tuned = {"block": blk, "index_mode": mode, "rhs_tile": tile, "z_chunk": zc, "smem_links": sm}
+            vals = [int(v) for v in args.launch.split(",")] + [0, 0]
+            blk, mode, tile, zc, sm, spt = vals[:6]
+            ctx.set_launch(prec, n, blk, mode, tile, zc, sm, spt)
+            tuned = {"block": blk, "index_mode": mode, "rhs_tile": tile, "z_chunk": zc, "smem_links": sm,
+                     "sites_per_thread": spt}
         inp = ctx.empty_half(prec, n)
         inp.zero_()
         out = ctx.empty_half(prec, n)
@@ -635,7 +636,8 @@ def main():
     ap.add_argument("--links", type=int, default=18, choices=[18, 12])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--tune", action="store_true", help="operator workload: autotune the launch first")
-    ap.add_argument("--launch", default=None, help="operator workload: block,index_mode,rhs_tile,z_chunk[,smem]")
+    ap.add_argument("--launch", default=None,
+                    help="operator workload: block,index_mode,rhs_tile,z_chunk[,smem[,sites_per_thread]]")
     ap.add_argument("--lattice", default=None,
                     help="LxxLyxLzxT for the operator workload (default 32x32x32x64); used for small profiling cases")
     args = ap.parse_args()

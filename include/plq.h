@@ -364,11 +364,15 @@ typedef struct {
     double us_per_launch; /* measured time of one half-lattice application                 */
     int from_cache;       /* 1 if the choice came from the cache file                      */
     int candidates;       /* configurations timed                                          */
+    int sites_per_thread; /* grid size: 0 one wave of resident blocks, each thread walking
+                             its share of the sites; k > 0 enough blocks for k sites (site
+                             blocks, with smem_links) per thread                           */
 } plq_tune_result;
 
 /* Autotuner of the hopping kernel's launch for precision `prec` and `nrhs`
  * right-hand sides: times every threads-per-block value in {64, 96, 128, 192,
- * 256} with neighbour indices computed inline from the coordinates and read
+ * 256, 512, 1024} that the kernel can launch (registers x threads within the
+ * SM's register file and the kernel's launch bound) with neighbour indices computed inline from the coordinates and read
  * from a precomputed per-site table (the pointer-array addressing the paper
  * describes for out-of-order site access, Sec. 2.2), and for nrhs > 1 (FP32
  * and FP16 storage) with 2 or 4 right-hand sides per thread (register tiles
@@ -378,7 +382,8 @@ typedef struct {
  * copied ahead asynchronously, the GPU counterpart of the paper's software
  * prefetch, Sec. 2.2), and with the sites walked in z-chunks of 8 or 4 planes (time
  * inside a chunk, which keeps the data reused through the time direction
- * within L2 for large multi-RHS fields), and keeps the fastest in
+ * within L2 for large multi-RHS fields), then the fastest of these with 1, 2,
+ * 4 or 8 sites per thread against its one-wave grid, and keeps the fastest in
  * the context for every later operator and solver call of that precision.
  * cache_path (NULL: the PLQ_TUNE_CACHE environment variable, if set) names a
  * text file keyed by GPU name, lattice, precision, link format and nrhs: a
@@ -388,12 +393,13 @@ typedef struct {
 PLQ_API plq_status plq_autotune(plq_ctx *ctx, int prec, int nrhs, const char *cache_path, plq_tune_result *res);
 
 /* Set the hopping launch of (prec, nrhs) by hand: block = threads per block
- * (0 = library default, else a multiple of 32 up to 256), index_mode 0 or 1,
+ * (0 = library default, else a multiple of 32 up to 1024; a block the kernel
+ * cannot launch makes the operator calls return PLQ_ERR_ARG), index_mode 0 or 1,
  * rhs_tile 1, 2 or 4 (dividing nrhs), z_chunk 0 or a divisor of Lz and
  * smem_links 0..3 (nrhs > 1, FP32/FP16; with 1, rhs_tile 1 or 2; with 2 or 3,
- * rhs_tile 1), as above. */
+ * rhs_tile 1) and sites_per_thread 0..64, as above. */
 PLQ_API plq_status plq_set_launch(plq_ctx *ctx, int prec, int nrhs, int block, int index_mode, int rhs_tile,
-                                  int z_chunk, int smem_links);
+                                  int z_chunk, int smem_links, int sites_per_thread);
 
 /* Two-pass schedule of the hopping operator through the auxiliary fields of
  * Eq. (2): pass 1 computes, at every input site y, theta+_mu(y) = (1 -

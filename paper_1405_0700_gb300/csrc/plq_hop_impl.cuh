@@ -605,7 +605,7 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
 template <int P, int R, int EPI, bool DAG, int RT, int NB>
 plq_status launch_mrhs_t(const HopArgs &a, cudaStream_t s, int block) {
     if (a.block > 0) block = a.block;
-    if (block <= 0 || block > 256) block = 128;
+    if (block <= 0 || block > 1024) block = 128;
     const int n = a.nrhs;
     const int tiles = n / RT;
     int spb = block / tiles > 0 ? block / tiles : 1;
@@ -625,15 +625,20 @@ plq_status launch_mrhs_t(const HopArgs &a, cudaStream_t s, int block) {
         cudaError_t e = cudaSuccess;
         if (smem > 48 * 1024)
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncAttributes fa{};
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem);
         if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(hop_mrhs)");
-        per_sm[spb][tiles].store(nb > 0 ? nb : 1, std::memory_order_relaxed);
+        if (threads > fa.maxThreadsPerBlock) nb = 0;
+        per_sm[spb][tiles].store(nb > 0 ? nb : -1, std::memory_order_relaxed);
     }
+    const int fit = per_sm[spb][tiles].load(std::memory_order_relaxed);
+    if (fit < 0) return set_error(PLQ_ERR_ARG, "a block of %d threads does not fit the multi-RHS kernel", threads);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long want = ((long long)a.lat.Vh + spb - 1) / spb;
-    long long cap = (long long)per_sm[spb][tiles].load(std::memory_order_relaxed) * sms;
+    const long long want = ((long long)a.lat.Vh + spb - 1) / spb;
+    long long cap = a.spt > 0 ? (want + a.spt - 1) / a.spt : (long long)fit * sms;
     if (EPI >= EPI_XPAY_NORM && cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
     const int grid = (int)(want < cap ? want : cap);
     if (grid <= 0) return PLQ_OK;
@@ -662,7 +667,7 @@ plq_status dispatch_mrhs(const HopArgs &a, int epi, cudaStream_t s, int block) {
 template <int P, int R, int EPI, bool DAG, bool TBL = false, int RT = 1>
 plq_status launch_hop_t(const HopArgs &a, cudaStream_t s, int block) {
     if (a.block > 0) block = a.block;
-    if (block <= 0 || block > 256) block = 128;
+    if (block <= 0 || block > 1024) block = 128;
     const int n = a.nrhs;
     const int tiles = n / RT;  // threads per site
     // sites per block: as many as fit in `block` threads, rounded so that the
@@ -674,7 +679,9 @@ plq_status launch_hop_t(const HopArgs &a, cudaStream_t s, int block) {
             break;
         }
     const int threads = tiles * spb;
-    static std::atomic<int> per_sm[257];  // occupancy per block size, filled on first use
+    // resident blocks per SM for each block size, filled on first use (-1:
+    // the block does not fit this kernel's registers or launch bound)
+    static std::atomic<int> per_sm[1025];
     constexpr int nreg = hop_reg_cap<P, R, EPI, TBL, RT>();
     auto kern = [] {
         if constexpr (nreg > 0) return hop_kernel_capped<P, R, EPI, DAG, TBL, RT, (nreg > 0 ? nreg : 255)>;
@@ -682,16 +689,23 @@ plq_status launch_hop_t(const HopArgs &a, cudaStream_t s, int block) {
     }();
     if (per_sm[threads].load(std::memory_order_relaxed) == 0) {
         int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0);
+        // the occupancy query does not apply the kernel's launch bound: the
+        // attribute's thread limit covers both it and the registers
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0);
         if (e != cudaSuccess) return cuda_error(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(hop)");
-        per_sm[threads].store(nb > 0 ? nb : 1, std::memory_order_relaxed);
+        if (threads > fa.maxThreadsPerBlock) nb = 0;
+        per_sm[threads].store(nb > 0 ? nb : -1, std::memory_order_relaxed);
     }
+    const int fit = per_sm[threads].load(std::memory_order_relaxed);
+    if (fit < 0) return set_error(PLQ_ERR_ARG, "a block of %d threads does not fit the hopping kernel", threads);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int i_end = a.site_end < 0 ? a.lat.Vh : a.site_end;
-    long long want = ((long long)(i_end - a.site_begin) + spb - 1) / spb;
-    long long cap = (long long)per_sm[threads].load(std::memory_order_relaxed) * sms;
+    const long long want = ((long long)(i_end - a.site_begin) + spb - 1) / spb;
+    long long cap = a.spt > 0 ? (want + a.spt - 1) / a.spt : (long long)fit * sms;
     if (EPI >= EPI_XPAY_NORM && cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
     const int grid = (int)(want < cap ? want : cap);
     if (grid <= 0) return PLQ_OK;

@@ -110,6 +110,7 @@ struct TuneEntry {
     int rhs_tile = 1;    // right-hand sides per thread
     int zc = 0;          // z-chunk site order (0 = natural)
     int smem_links = 0;  // multi-RHS links staged in shared memory
+    int spt = 0;         // sites per thread: 0 = one wave of resident blocks
     float us = 0.f;
 };
 
@@ -204,6 +205,10 @@ struct HopArgs {
     int site_begin = 0;   // output sites [site_begin, site_end) of the parity;
     int site_end = -1;    // -1: up to Vh
     int smem_links = 0;   // multi-RHS: stage each block's links in shared memory
+    // Grid size: 0 = as many blocks as are resident on the GPU at once (each
+    // thread walks its share of the sites); k > 0 = enough blocks for k sites
+    // (site blocks of the multi-RHS kernel) per thread.
+    int spt = 0;
 };
 
 // Launch the hopping kernel for (prec, link reals, epilogue).  block = 0 picks

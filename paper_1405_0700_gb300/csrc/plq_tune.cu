@@ -49,15 +49,20 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         char k[600];
-        int block = 0, mode = 0, tile = 1, zc = 0, sm = 0;
+        int block = 0, mode = 0, tile = 1, zc = 0, sm = 0, spt = 0;
         float us = 0;
-        if (sscanf(line, "%599s %d %d %d %d %d %f", k, &block, &mode, &tile, &zc, &sm, &us) == 7 && key == k &&
-            sm >= 0 && sm <= 3) {
+        // key block index_mode rhs_tile z_chunk smem_links us [sites_per_thread]
+        const int got = sscanf(line, "%599s %d %d %d %d %d %f %d", k, &block, &mode, &tile, &zc, &sm, &us, &spt);
+        const bool valid = (block == 0 || (block >= 32 && block <= 1024 && block % 32 == 0)) && (mode == 0 || mode == 1) &&
+                           (tile == 1 || tile == 2 || tile == 4) && zc >= 0 && sm >= 0 && sm <= 3 && spt >= 0 &&
+                           spt <= 64;
+        if (got >= 7 && key == k && valid) {
             e->block = block;
             e->index_mode = mode;
             e->rhs_tile = tile;
             e->zc = zc;
             e->smem_links = sm;
+            e->spt = spt;
             e->us = us;
             found = true;  // last entry wins
         }
@@ -69,8 +74,8 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
 void cache_store(const char *path, const std::string &key, const TuneEntry &e) {
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %d %d %d %.3f\n", key.c_str(), e.block, e.index_mode, e.rhs_tile, e.zc, e.smem_links,
-            e.us);
+    fprintf(f, "%s %d %d %d %d %d %.3f %d\n", key.c_str(), e.block, e.index_mode, e.rhs_tile, e.zc, e.smem_links,
+            e.us, e.spt);
     fclose(f);
 }
 
@@ -96,6 +101,7 @@ void apply_tune(const Ctx *c, int prec, int nrhs, HopArgs &a) {
     a.rhs_tile = (e.rhs_tile > 1 && nrhs % e.rhs_tile == 0) ? e.rhs_tile : 1;
     a.zc = (e.zc > 0 && c->lat.L[3] % e.zc == 0) ? e.zc : 0;
     a.smem_links = nrhs > 1 ? e.smem_links : 0;
+    a.spt = e.spt;
 }
 
 }  // namespace plq
@@ -122,6 +128,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
             res->rhs_tile = best.rhs_tile;
             res->z_chunk = best.zc;
             res->smem_links = best.smem_links;
+            res->sites_per_thread = best.spt;
             res->us_per_launch = best.us;
             res->from_cache = 1;
         }
@@ -142,7 +149,9 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
     cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    static const int blocks[] = {64, 96, 128, 192, 256};
+    // block sizes a kernel cannot launch (registers x threads above the SM's
+    // register file, or above its launch bound) are skipped
+    static const int blocks[] = {64, 96, 128, 192, 256, 512, 1024};
     plq_status st = PLQ_OK;
     best.us = 1e30f;
     int tried = 0;
@@ -170,44 +179,67 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
         if (prec != PLQ_F64 && nrhs > 1 && z == 0) cands[nc++] = {0, 1, z, 3};
         if (prec != PLQ_F64 && nrhs > 1 && nrhs % 2 == 0) cands[nc++] = {0, 2, z, 1};
     }
+    // time one configuration; PLQ_ERR_ARG from the first launch means that
+    // the block does not fit the kernel (us stays negative)
+    auto time_cfg = [&](const TuneEntry &t, float *us_out) -> plq_status {
+        HopArgs a;
+        a.in = in;
+        a.out = out;
+        a.gauge = c->gauge[prec].ptr;
+        a.gblock = c->gauge[prec].block;
+        a.out_parity = 0;
+        a.nrhs = nrhs;
+        a.lat = c->lat;
+        a.block = t.block;
+        a.nbr = t.index_mode ? c->nbr[0] : nullptr;
+        a.rhs_tile = t.rhs_tile;
+        a.zc = t.zc;
+        a.smem_links = t.smem_links;
+        a.spt = t.spt;
+        *us_out = -1.f;
+        plq_status r = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
+        if (r == PLQ_ERR_ARG) return PLQ_OK;
+        if (r == PLQ_OK) r = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
+        cudaEventRecord(e0, s);
+        for (int q = 0; q < reps && r == PLQ_OK; ++q) r = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
+        cudaEventRecord(e1, s);
+        if (r != PLQ_OK) return r;
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) return cuda_error(ce, "autotune timing");
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *us_out = ms * 1000.f / reps;
+        ++tried;
+        return PLQ_OK;
+    };
     for (int ci = 0; ci < nc && st == PLQ_OK; ++ci) {
-        const int mode = cands[ci].mode;
         for (int b : blocks) {
-            HopArgs a;
-            a.in = in;
-            a.out = out;
-            a.gauge = c->gauge[prec].ptr;
-            a.gblock = c->gauge[prec].block;
-            a.out_parity = 0;
-            a.nrhs = nrhs;
-            a.lat = c->lat;
-            a.block = b;
-            a.nbr = mode ? c->nbr[0] : nullptr;
-            a.rhs_tile = cands[ci].tile;
-            a.zc = cands[ci].zc;
-            a.smem_links = cands[ci].smem;
-            for (int w = 0; w < 2 && st == PLQ_OK; ++w) st = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < reps && st == PLQ_OK; ++r) st = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
-            cudaEventRecord(e1, s);
+            TuneEntry t;
+            t.block = b;
+            t.index_mode = cands[ci].mode;
+            t.rhs_tile = cands[ci].tile;
+            t.zc = cands[ci].zc;
+            t.smem_links = cands[ci].smem;
+            float us = -1.f;
+            st = time_cfg(t, &us);
             if (st != PLQ_OK) break;
-            e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) {
-                st = cuda_error(e, "autotune timing");
-                break;
+            if (us >= 0.f && us < best.us) {
+                t.us = us;
+                best = t;
             }
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const float us = ms * 1000.f / reps;
-            ++tried;
-            if (us < best.us) {
-                best.us = us;
-                best.block = b;
-                best.index_mode = mode;
-                best.rhs_tile = cands[ci].tile;
-                best.zc = cands[ci].zc;
-                best.smem_links = cands[ci].smem;
-            }
+        }
+    }
+    // sites per thread: a grid sized for k sites (site blocks) per thread
+    // against the one-wave grid of the sweep above
+    for (int k : {1, 2, 4, 8}) {
+        if (st != PLQ_OK) break;
+        TuneEntry t = best;
+        t.spt = k;
+        float us = -1.f;
+        st = time_cfg(t, &us);
+        if (st == PLQ_OK && us >= 0.f && us < best.us) {
+            t.us = us;
+            best = t;
         }
     }
     cudaEventDestroy(e0);
@@ -225,6 +257,7 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
         res->rhs_tile = best.rhs_tile;
         res->z_chunk = best.zc;
         res->smem_links = best.smem_links;
+        res->sites_per_thread = best.spt;
         res->us_per_launch = best.us;
         res->from_cache = 0;
         res->candidates = tried;
@@ -233,12 +266,14 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
 }
 
 extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, int index_mode, int rhs_tile,
-                                     int z_chunk, int smem_links) {
+                                     int z_chunk, int smem_links, int sites_per_thread) {
     if (!c) return set_error(PLQ_ERR_ARG, "null context");
     if (!valid_prec(prec)) return set_error(PLQ_ERR_ARG, "bad precision %d", prec);
     if (nrhs < 1 || nrhs > PLQ_MAX_RHS) return set_error(PLQ_ERR_ARG, "nrhs must be in 1..%d", PLQ_MAX_RHS);
-    if (block != 0 && (block < 32 || block > 256 || (block % 32)))
-        return set_error(PLQ_ERR_ARG, "block must be 0 or a multiple of 32 in 32..256");
+    if (block != 0 && (block < 32 || block > 1024 || (block % 32)))
+        return set_error(PLQ_ERR_ARG, "block must be 0 or a multiple of 32 in 32..1024");
+    if (sites_per_thread < 0 || sites_per_thread > 64)
+        return set_error(PLQ_ERR_ARG, "sites_per_thread must be in 0..64");
     if (index_mode != 0 && index_mode != 1) return set_error(PLQ_ERR_ARG, "index_mode must be 0 or 1");
     if (rhs_tile != 1 && rhs_tile != 2 && rhs_tile != 4) return set_error(PLQ_ERR_ARG, "rhs_tile must be 1, 2 or 4");
     if (nrhs % rhs_tile) return set_error(PLQ_ERR_ARG, "rhs_tile must divide nrhs");
@@ -253,6 +288,7 @@ extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, 
     c->tune[prec][nrhs].rhs_tile = rhs_tile;
     c->tune[prec][nrhs].zc = z_chunk;
     c->tune[prec][nrhs].smem_links = smem_links;
+    c->tune[prec][nrhs].spt = sites_per_thread;
     ++c->tune_version;
     return PLQ_OK;
 }

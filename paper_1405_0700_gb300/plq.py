@@ -60,6 +60,7 @@ class TuneResult(ctypes.Structure):
         ("us_per_launch", ctypes.c_double),
         ("from_cache", ctypes.c_int),
         ("candidates", ctypes.c_int),
+        ("sites_per_thread", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -129,7 +130,7 @@ SIGNATURES = {
     "plq_measure_fma_rate": (_c_int, [_c_int, _c_int, ctypes.POINTER(ctypes.c_double)]),
     "plq_schur_apply_noalloc": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, _c_int, _vp]),
     "plq_autotune": (_c_int, [_vp, _c_int, _c_int, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
-    "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int]),
+    "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int]),
 }
 
 _lib = None
@@ -335,8 +336,10 @@ class Context:
         check(lib().plq_autotune(self._h, prec_of(prec), nrhs, path, ctypes.byref(r)))
         return r.as_dict()
 
-    def set_launch(self, prec, nrhs=1, block=0, index_mode=0, rhs_tile=1, z_chunk=0, smem_links=0):
-        check(lib().plq_set_launch(self._h, prec_of(prec), nrhs, block, index_mode, rhs_tile, z_chunk, smem_links))
+    def set_launch(self, prec, nrhs=1, block=0, index_mode=0, rhs_tile=1, z_chunk=0, smem_links=0,
+                   sites_per_thread=0):
+        check(lib().plq_set_launch(self._h, prec_of(prec), nrhs, block, index_mode, rhs_tile, z_chunk, smem_links,
+                                   sites_per_thread))
 
     # ------------------------------------------------------------ solvers
     def _solve(self, fn, x, b, kappa, tol, maxit, inner_prec, delta, use_x0, check_every, stream, raise_on_error,

@@ -57,3 +57,48 @@ def test_argument_errors_without_gpu(lib):
     assert lib.plq_cg_solve(None, None, None, 0.1, None, None, None) == plq.PLQ_ERR_ARG
     assert lib.plq_finalize(None) == plq.PLQ_OK
     assert lib.plq_version() >= 10000
+
+
+def header_text():
+    return "\n".join(open(os.path.join(ROOT, "include", h)).read()
+                     for h in sorted(os.listdir(os.path.join(ROOT, "include"))) if h.endswith(".h"))
+
+
+def strip_comments(txt):
+    return re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+
+
+C_TYPES = {"int": ctypes.c_int, "double": ctypes.c_double}
+
+
+def header_structs():
+    """{typedef name: [(field, ctype), ...]} for the plain structs of the header."""
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(plq_\w+)\s*;", strip_comments(header_text()), re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            typ, field = decl.rsplit(None, 1)
+            fields.append((field, C_TYPES[typ.strip()]))
+        out[name] = fields
+    return out
+
+
+@pytest.mark.parametrize("cname,cls", [("plq_solver_params", plq.SolverParams), ("plq_solve_info", plq.SolveInfo),
+                                       ("plq_batch_info", plq.BatchInfo), ("plq_tune_result", plq.TuneResult)])
+def test_binding_structs_match_header(cname, cls):
+    """Field names, types and order of every ctypes struct equal the header's."""
+    assert header_structs()[cname] == list(cls._fields_)
+
+
+def test_binding_argument_counts_match_header():
+    """Each declared function takes as many arguments as the binding passes."""
+    txt = strip_comments(header_text())
+    decls = re.findall(r"PLQ_API\s+[\w\s\*]+?\b(plq_\w+)\s*\(([^)]*)\)\s*;", txt)
+    assert decls
+    for name, args in decls:
+        args = args.strip()
+        n = 0 if args in ("", "void") else args.count(",") + 1
+        assert len(plq.SIGNATURES[name][1]) == n, name

@@ -261,14 +261,70 @@ def test_autotune_and_cache(tmp_path):
     with Context(dims) as ctx:
         ctx.gauge_upload(U, 18, F32)
         r = ctx.autotune(F32, 1, cache_path=cache)
-        assert r["from_cache"] == 0 and r["candidates"] >= 10 and r["block"] in (64, 96, 128, 192, 256)
+        assert r["from_cache"] == 0 and r["candidates"] >= 10
+        assert r["block"] in (64, 96, 128, 192, 256, 512) and r["sites_per_thread"] in (0, 1, 2, 4, 8)
         got = gpu_hopping_full(ctx, phi, F32)  # runs with the tuned launch
         assert rel(got, W.hopping(U, phi)) <= TOL[F32]
     with Context(dims) as ctx:
         ctx.gauge_upload(U, 18, F32)
         r2 = ctx.autotune(F32, 1, cache_path=cache)
-        assert r2["from_cache"] == 1 and r2["block"] == r["block"] and r2["index_mode"] == r["index_mode"]
+        assert r2["from_cache"] == 1
+        for k in ("block", "index_mode", "rhs_tile", "z_chunk", "smem_links", "sites_per_thread"):
+            assert r2[k] == r[k], k
     assert open(cache).read().count("\n") == 1
+
+
+def test_autotune_cache_ignores_invalid_lines(tmp_path):
+    """A cache line with an out-of-range field is skipped (the tuner times instead);
+    a line in the older seven-field form reads as one wave of resident blocks."""
+    dims = (8, 4, 4, 4)
+    U = S.gauge_field(dims, 0.3, 11)
+    cache = tmp_path / "tune.txt"
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F32)
+        r = ctx.autotune(F32, 1, cache_path=str(cache))
+    key = cache.read_text().split()[0]
+    cache.write_text(f"{key} 100 0 1 0 0 1.0\n")  # block 100: not a multiple of 32
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F32)
+        assert ctx.autotune(F32, 1, cache_path=str(cache))["from_cache"] == 0
+    cache.write_text(f"{key} 64 0 1 0 0 1.0\n")
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F32)
+        r3 = ctx.autotune(F32, 1, cache_path=str(cache))
+        assert r3["from_cache"] == 1 and r3["block"] == 64 and r3["sites_per_thread"] == 0
+
+
+@pytest.mark.parametrize("prec,reals,nrhs,block,sm,spt", [
+    (F32, 18, 1, 512, 0, 0), (F32, 18, 1, 512, 0, 1), (F32, 12, 1, 128, 0, 4), (F16, 12, 1, 64, 0, 8),
+    (F64, 18, 1, 128, 0, 2), (F32, 18, 12, 96, 1, 2), (F16, 12, 5, 512, 3, 1), (F32, 12, 4, 256, 0, 3)])
+def test_block_sizes_and_sites_per_thread(prec, reals, nrhs, block, sm, spt):
+    """Blocks above 256 threads (where the kernel's registers allow) and grids sized for
+    k sites per thread, including grids that leave a ragged last block."""
+    dims = (6, 4, 4, 6)
+    U = S.gauge_field(dims, 0.3, 18)
+    phis = np.stack([S.gaussian_spinor(dims, 400 + r) for r in range(nrhs)])
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, reals, prec)
+        ctx.set_launch(prec, nrhs, block, 0, 1, 0, sm, spt)
+        got = gpu_hopping_full(ctx, phis if nrhs > 1 else phis[0], prec, nrhs).reshape(phis.shape)
+    for r in range(nrhs):
+        assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], r
+
+
+def test_block_that_does_not_fit_is_an_argument_error():
+    """1024 threads x 80 registers exceed the SM's register file: the operator call
+    returns PLQ_ERR_ARG (nothing launched) and the context keeps working."""
+    dims = (4, 4, 4, 4)
+    U, phi = S.gauge_and_spinor(dims, 0.3, 19)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F32)
+        ctx.set_launch(F32, 1, 1024, 0, 1, 0, 0, 0)
+        with pytest.raises(PLQError) as e:
+            gpu_hopping_full(ctx, phi, F32)
+        assert e.value.status == plq.PLQ_ERR_ARG
+        ctx.set_launch(F32, 1, 0, 0, 1, 0, 0, 0)
+        assert rel(gpu_hopping_full(ctx, phi, F32), W.hopping(U, phi)) <= TOL[F32]
 
 
 def test_host_entry_point_follows_gauge_format_change():

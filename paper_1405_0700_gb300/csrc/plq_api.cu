@@ -303,6 +303,35 @@ plq_status plq_hopping_eo(plq_ctx *c, int out_parity, void *out, const void *in,
 
 namespace {
 
+constexpr int kMaxHostSlabs = 64;
+
+// Time-slice boundaries bound[0..K] (bound[0] = 0, bound[K] = T) of the host
+// pipeline's slabs: ramps of 1, 1, 2, 4, ... slices (each below T/8) at both
+// ends, slabs of T/8 slices between them; returns K.
+int host_slab_bounds(int T, int *bound) {
+    const int m = T / 8 > 1 ? T / 8 : 1;
+    int ramp[16], nr = 0, rs = 0;
+    for (int v = 1; nr < 16;) {
+        if (v >= m || 2 * (rs + v) > T) break;
+        ramp[nr++] = v;
+        rs += v;
+        if (nr >= 2) v *= 2;
+    }
+    int sizes[kMaxHostSlabs], K = 0;
+    for (int q = 0; q < nr; ++q) sizes[K++] = ramp[q];
+    int mid = T - 2 * rs;
+    while (mid > 0 && K < kMaxHostSlabs - nr) {
+        const int v = mid < m ? mid : m;
+        sizes[K++] = v;
+        mid -= v;
+    }
+    if (mid > 0) sizes[K - 1] += mid;  // unreachable for T <= 8 * kMaxHostSlabs / 2
+    for (int q = nr - 1; q >= 0; --q) sizes[K++] = ramp[q];
+    bound[0] = 0;
+    for (int k = 0; k < K; ++k) bound[k + 1] = bound[k] + sizes[k];
+    return K;
+}
+
 // Enqueue the host pipeline of plq_hopping_eo_host.  `origin` is the stream
 // the copies in start from and that ends ordered after the last copy out.
 plq_status enqueue_host_pipeline(plq_ctx *c, int out_parity, char *hout, const char *hin, int prec, int nrhs,
@@ -315,13 +344,18 @@ plq_status enqueue_host_pipeline(plq_ctx *c, int out_parity, char *hout, const c
     // output slabs stream back on the other engine while later slabs compute.
     const int T = c->lat.L[0];
     const int slab = c->lat.Vh / T;  // checkerboard sites per time slice
-    // 16 slabs: measured 0.84 ms for 32^3x64 FP32 (100 MB each way) against
-    // 0.86 ms with 8 and 0.98 ms with 4; the host link itself moves the same
-    // bytes in 0.59 ms with both directions busy, 0.70 ms as chunked copies
-    const int K = T < 16 ? T : 16;
+    // Slab sizes: each copy costs ~6 us on top of its bytes, while the first
+    // output waits for three input slabs and the last copy out follows the
+    // last compute.  So the slabs grow 1, 1, 2, 4, ... time slices up to T/8
+    // and shrink the same way at the end: short fill and drain, few copies.
+    // 32^3x64 FP32 (100 MB each way): 0.813 ms, against 0.829 ms with 16
+    // equal slabs; the link moves the same bytes in 0.60 ms as one copy in
+    // each direction.
+    int bound[kMaxHostSlabs + 1];
+    const int K = host_slab_bounds(T, bound);
     const size_t n = (size_t)nrhs, VhN = (size_t)c->lat.Vh * n;
     const int nplanes = prec == PLQ_F64 ? 12 : prec == PLQ_F32 ? 6 : 3;
-    auto chunk_t0 = [&](int k) { return (int)((long long)T * k / K); };
+    auto chunk_t0 = [&](int k) { return bound[k]; };
     auto copy_chunk = [&](char *dst, const char *src, int k, cudaMemcpyKind kind, cudaStream_t s) -> cudaError_t {
         const size_t e0 = (size_t)chunk_t0(k) * slab * n, e1 = (size_t)chunk_t0(k + 1) * slab * n;
         cudaError_t e = cudaMemcpy2DAsync(dst + e0 * 16, VhN * 16, src + e0 * 16, VhN * 16, (e1 - e0) * 16, nplanes,

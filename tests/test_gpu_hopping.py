@@ -327,6 +327,28 @@ def test_block_that_does_not_fit_is_an_argument_error():
         assert rel(gpu_hopping_full(ctx, phi, F32), W.hopping(U, phi)) <= TOL[F32]
 
 
+@pytest.mark.parametrize("T", [2, 6, 24, 40, 96])
+def test_host_entry_point_slab_schedules(T):
+    """Time extents whose slab schedules differ (one slice per slab; ramps of 1, 1, 2
+    ... slices at both ends with T/8 slices between, and a remainder slab): the host
+    pipeline equals plq_hopping_eo bit for bit on both parities."""
+    dims = (T, 4, 2, 2)
+    U = S.gauge_field(dims, 0.3, 20)
+    phi = S.gaussian_spinor(dims, 21)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F32)
+        full = ctx.to_device(phi, F32)
+        e_in, o_in = ctx.halves(full, F32)
+        dev_out = ctx.empty_half(F32)
+        for parity, src in ((0, o_in), (1, e_in)):
+            ctx.hopping_eo(parity, dev_out, src, F32)
+            host_in = src.cpu().pin_memory()
+            host_out = torch.zeros_like(host_in).pin_memory()
+            ctx.hopping_eo_host(parity, host_out, host_in, F32)
+            torch.cuda.synchronize()
+            assert torch.equal(host_out, dev_out.cpu()), parity
+
+
 def test_host_entry_point_follows_gauge_format_change():
     dims = (8, 4, 4, 4)
     U, phi = S.gauge_and_spinor(dims, 0.3, 12)

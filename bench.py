@@ -150,20 +150,23 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle timing
-def oracle_sample(U, phi, sites, reps_min=1, seconds=10.0, max_reps=1000):
-    """Time the C oracle on `sites` output sites, repeated until ~seconds pass."""
+def oracle_sample(U, phi, sites, seconds=10.0, min_reps=5, max_reps=1000, nthreads=0):
+    """Time the C oracle on `sites` output sites, one repetition at a time, until
+    ~seconds pass and at least min_reps ran; returns (median seconds per
+    repetition, repetitions, elapsed seconds, threads used)."""
     from oracle import c_oracle as C
 
-    C.hopping_sites(U, phi, sites[:1024])  # load and warm
-    t0 = time.perf_counter()
-    reps = 0
+    C.hopping_sites(U, phi, sites[:1024], nthreads=nthreads)  # load and warm
+    times = []
+    t_start = time.perf_counter()
     while True:
-        C.hopping_sites(U, phi, sites)
-        reps += 1
-        el = time.perf_counter() - t0
-        if (el >= seconds and reps >= reps_min) or reps >= max_reps:
+        t0 = time.perf_counter()
+        C.hopping_sites(U, phi, sites, nthreads=nthreads)
+        times.append(time.perf_counter() - t0)
+        el = time.perf_counter() - t_start
+        if (el >= seconds and len(times) >= min_reps) or len(times) >= max_reps:
             break
-    return reps, el, C.threads()
+    return float(np.median(times)), len(times), el, C.threads(nthreads)
 
 
 def output_sites(dims, parity):
@@ -765,11 +768,18 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         sites = output_sites(dims, 0)
-        reps, el, cores = oracle_sample(U, phi, sites, seconds=10.0)
-        cpu = {"value": FLOP_PER_SITE * len(sites) * reps / el / 1e9, "unit": "GFLOP/s", "cores": cores,
+        med, reps, el, cores = oracle_sample(U, phi, sites, seconds=10.0)
+        # one thread last (the OpenMP thread count persists; restored after)
+        med1, reps1, el1, _ = oracle_sample(U, phi, sites, seconds=5.0, nthreads=1)
+        from oracle import c_oracle as C
+
+        C.threads(cores)
+        cpu = {"value": FLOP_PER_SITE * len(sites) / med / 1e9, "unit": "GFLOP/s", "cores": cores,
                "kind": "oracle",
                "sample": f"C oracle (FP64 Eq. (1) site loop, OpenMP) over all {len(sites)} even output sites of the "
-                         f"same 32^3x64 half-application, {reps} repetitions in {el:.1f}s"}
+                         f"same 32^3x64 half-application, median of {reps} repetitions ({el:.1f}s)",
+               "single_thread": {"value": FLOP_PER_SITE * len(sites) / med1 / 1e9, "unit": "GFLOP/s", "cores": 1,
+                                 "sample": f"the same, one thread, median of {reps1} repetitions ({el1:.1f}s)"}}
 
     traffic, _ = measured_traffic() if dims == HOP_DIMS else (None, None)
     if rank == 0:

@@ -458,6 +458,21 @@ def propagator_section(torch, local_rank, quick):
             "max_true_rel_residual": max(i.true_rel_residual for i in infos),
             "status": [i.status for i in infos]}
         log(f"[bench] batched CG x{n}, float-float residuals: {el_df:.2f}s")
+        # FP16-storage inner iterations (12-real links), float-float residuals
+        ctx.gauge_upload(U, 12, F16)
+        ctx.autotune(F16, n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = ctx.cg_solve_multi(x, bd, kappa, n, tol=1e-10, inner_prec=F16, maxit=3000, raise_on_error=False,
+                                   residual_prec=DF64)
+        torch.cuda.synchronize()
+        el_h = time.perf_counter() - t0
+        out["batched_cg_mixed_f16_dfres"] = {
+            "seconds": el_h, "seconds_per_rhs": el_h / n,
+            "iterations": [i.iterations for i in infos], "reliable_updates": infos[0].n_reliable,
+            "max_true_rel_residual": max(i.true_rel_residual for i in infos),
+            "status": [i.status for i in infos]}
+        log(f"[bench] batched CG x{n}, FP16 inner, float-float residuals: {el_h:.2f}s")
         # the same right-hand sides one at a time (single-RHS solver, same inner precision)
         singles = []
         for r in range(n if not quick else 2):

@@ -169,6 +169,12 @@ struct Spinor<PLQ_F16> {
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+        // A site whose largest component is below the smallest normal float
+        // (2^-126) is stored as zero: 1/m would overflow to infinity.  Such
+        // sites occur at the edge of the support of the early Krylov vectors
+        // of a point source, many orders of magnitude below the field's norm.
+        constexpr float kMinNormal = 1.17549435e-38f;
+        if (!(m >= kMinNormal)) m = 0.f;
         const float inv = m > 0.f ? 1.0f / m : 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {

@@ -349,6 +349,29 @@ def test_host_entry_point_slab_schedules(T):
             assert torch.equal(host_out, dev_out.cpu()), parity
 
 
+def test_fp16_storage_of_values_down_to_the_subnormal_range():
+    """Sites whose largest component spans 1 .. 1e-44: FP16 storage keeps every site
+    with a normal-range maximum to half-precision accuracy, stores sites below 2^-126 as
+    zero (no infinities or NaNs), and the operator on such a field stays within the
+    FP16 tolerance."""
+    dims = (8, 4, 4, 4)
+    U = S.gauge_field(dims, 0.3, 23)
+    phi = S.gaussian_spinor(dims, 24)
+    scale = 10.0 ** (-np.arange(S.volume(dims)) % 46)  # 1, 0.1, ..., 1e-45 per site
+    phi = phi * scale.reshape(S.lattice_shape(dims) + (1, 1))
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 12, F16)
+        back = ctx.to_host(ctx.to_device(phi, F16), F16)
+        got = gpu_hopping_full(ctx, phi, F16)
+    assert np.all(np.isfinite(back)) and np.all(np.isfinite(got))
+    site_max = np.abs(phi).max(axis=(-2, -1))
+    big = site_max >= 2.0 ** -126
+    err = np.abs(back - phi).max(axis=(-2, -1))
+    assert np.all(err[big] <= 1e-3 * site_max[big])
+    assert np.all(back[~big] == 0)
+    assert rel(got, W.hopping(U, phi)) <= TOL[F16]
+
+
 def test_host_entry_point_follows_gauge_format_change():
     dims = (8, 4, 4, 4)
     U, phi = S.gauge_and_spinor(dims, 0.3, 12)

@@ -158,6 +158,21 @@ def test_multi_rhs_point_sources(method, inner):
         assert abs(infos[r].true_rel_residual - res) < 1e-11
 
 
+@pytest.mark.parametrize("method", ["cg", "bicgstab"])
+def test_fp16_inner_point_source_long_lattice(method):
+    """A point source on a 192 x 2^3 lattice: the support of the early Krylov vectors
+    grows along t with values falling by ~2 kappa per site, so before it wraps around
+    its edge passes through FP32's subnormal range; the FP16 inner iterations must store
+    those sites (as zero) without producing infinities or NaNs."""
+    dims = (192, 2, 2, 2)
+    kappa = 0.115
+    srcs = [S.point_source(dims, 0, c) for c in range(3)]
+    U, b, x, infos = run_multi(method, dims, 0.25, 22, kappa, F16, srcs)
+    for r in range(3):
+        res = oracle_residual(U, b[r], x[r], kappa)
+        assert res <= 1e-10, (r, res, infos[r].as_dict())
+
+
 @pytest.mark.parametrize("tile,sm", [(2, 0), (4, 0), (1, 1), (2, 1), (1, 2), (1, 3)])
 def test_multi_rhs_cg_with_rhs_tiles(tile, sm):
     dims = (8, 4, 4, 8)

@@ -357,7 +357,7 @@ def test_fp16_storage_of_values_down_to_the_subnormal_range():
     dims = (8, 4, 4, 4)
     U = S.gauge_field(dims, 0.3, 23)
     phi = S.gaussian_spinor(dims, 24)
-    scale = 10.0 ** (-np.arange(S.volume(dims)) % 46)  # 1, 0.1, ..., 1e-45 per site
+    scale = np.power(10.0, -(np.arange(S.volume(dims)) % 46))  # 1, 0.1, ..., 1e-45 per site
     phi = phi * scale.reshape(S.lattice_shape(dims) + (1, 1))
     with Context(dims) as ctx:
         ctx.gauge_upload(U, 12, F16)

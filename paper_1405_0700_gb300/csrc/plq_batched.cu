@@ -231,12 +231,12 @@ __device__ void hop_site(const Lattice &lat, const void *g, size_t gb, int par, 
             hop_dir<P, R, 2, false, false>(a, geo, i, 0, acc);
             hop_dir<P, R, 3, false, false>(a, geo, i, 0, acc);
         }
-        return;
-    }
-    // FP64 phases (bound by the FP64 pipe): one run-time loop over the directions
+    } else {
+        // FP64 phases (bound by the FP64 pipe): one run-time loop over the directions
 #pragma unroll 1
-    for (int d = 0; d < 8; ++d)
-        hop_dir_rt<P, R>(lat, static_cast<const char *>(g), gb, par, dag, in, geo, i, d, acc);
+        for (int d = 0; d < 8; ++d)
+            hop_dir_rt<P, R>(lat, static_cast<const char *>(g), gb, par, dag, in, geo, i, d, acc);
+    }
 }
 
 template <class T>

@@ -189,6 +189,24 @@ def prec_of(p):
     return PREC_NAMES[p] if isinstance(p, str) else int(p)
 
 
+def spinor_shape(dims, nrhs=1):
+    """Shape of `nrhs` canonical spinor fields of lattice dims = (T, Lx, Ly, Lz)."""
+    T, Lx, Ly, Lz = dims
+    return ((nrhs,) if nrhs > 1 else ()) + (T, Lz, Ly, Lx, 4, 3)
+
+
+def read_spinors(path, dims, nrhs=1):
+    """Canonical complex128 spinor field(s) from a NumPy .npy file, checked against
+    the lattice and the number of right-hand sides."""
+    a = np.load(path, allow_pickle=False)
+    want = spinor_shape(dims, nrhs)
+    if a.shape != want:
+        raise ValueError(f"{path}: shape {a.shape}, expected {want} for lattice {tuple(dims)} and nrhs={nrhs}")
+    if a.dtype != np.complex128:
+        raise ValueError(f"{path}: dtype {a.dtype}, expected complex128")
+    return a
+
+
 class Context:
     """A lattice on one GPU: ``dims = (T, Lx, Ly, Lz)``, time boundary ``t_bc``."""
 
@@ -280,13 +298,22 @@ class Context:
         """Packed full field on the device -> canonical complex128 NumPy array."""
         import torch
 
-        T, Lx, Ly, Lz = self.dims
         out = torch.empty(nrhs * self.volume * 24, dtype=torch.float64, device=f"cuda:{self.device}")
         self.unpack_spinor(out, field, prec, nrhs, stream)
         torch.cuda.synchronize(self.device)
         a = out.cpu().numpy().view(np.complex128)
-        shape = (T, Lz, Ly, Lx, 4, 3)
-        return a.reshape(((nrhs,) if nrhs > 1 else ()) + shape)
+        return a.reshape(spinor_shape(self.dims, nrhs))
+
+    def save_field(self, path, field, prec, nrhs=1):
+        """Checkpoint: write a packed field to `path` as a NumPy .npy array of canonical
+        complex128 spinors (exact for FP64 fields); a solve resumes from it through
+        load_field and use_x0."""
+        np.save(path, self.to_host(field, prec, nrhs), allow_pickle=False)
+
+    def load_field(self, path, prec, nrhs=1):
+        """A new packed field of precision `prec` from a file written by save_field (or any
+        canonical complex128 array of this lattice's shape)."""
+        return self.to_device(read_spinors(path, self.dims, nrhs), prec, nrhs)
 
     # ------------------------------------------------------------ operators
     def hopping_eo(self, out_parity, out, inp, prec, nrhs=1, stream=None):

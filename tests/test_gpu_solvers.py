@@ -77,6 +77,31 @@ def test_resume_from_x0():
     assert info2.iterations < fresh.iterations
 
 
+def test_checkpoint_and_resume_in_a_new_context(tmp_path):
+    """A solve stopped by its iteration cap writes x to a .npy checkpoint; a new context
+    loads it (bit for bit) and resumes from it with use_x0 to the true residual 1e-10."""
+    dims = (8, 4, 4, 4)
+    U, b = S.gauge_and_spinor(dims, 0.3, 4)
+    kappa = 0.12
+    path = str(tmp_path / "x.npy")
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        bd = ctx.to_device(b, F64)
+        x = ctx.empty_full(F64)
+        info1 = ctx.cg_solve(x, bd, kappa, tol=1e-10, maxit=10, raise_on_error=False)
+        assert info1.status == plq.PLQ_ERR_NOT_CONVERGED
+        ctx.save_field(path, x, F64)
+        saved = ctx.to_host(x, F64)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        bd = ctx.to_device(b, F64)
+        x = ctx.load_field(path, F64)
+        assert np.array_equal(ctx.to_host(x, F64), saved)
+        ctx.cg_solve(x, bd, kappa, tol=1e-10, use_x0=True)
+        xs = ctx.to_host(x, F64)
+    assert oracle_residual(U, b, xs, kappa) <= 1e-10
+
+
 def test_maxit_returns_not_converged():
     with pytest.raises(PLQError) as e:
         run("cg", (8, 4, 4, 4), 0.3, 5, 0.12, F64, maxit=5)

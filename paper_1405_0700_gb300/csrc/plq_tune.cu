@@ -55,7 +55,7 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
         const int got = sscanf(line, "%599s %d %d %d %d %d %f %d", k, &block, &mode, &tile, &zc, &sm, &us, &spt);
         const bool valid = (block == 0 || (block >= 32 && block <= 1024 && block % 32 == 0)) && (mode == 0 || mode == 1) &&
                            (tile == 1 || tile == 2 || tile == 4) && zc >= 0 && sm >= 0 && sm <= 3 && spt >= 0 &&
-                           spt <= 64;
+                           spt <= 64 && !(sm >= 2 && tile != 1) && !(sm == 1 && tile == 4);
         if (got >= 7 && key == k && valid) {
             e->block = block;
             e->index_mode = mode;
@@ -281,6 +281,7 @@ extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, 
         return set_error(PLQ_ERR_ARG, "z_chunk must be 0 or divide Lz");
     if (smem_links < 0 || smem_links > 3) return set_error(PLQ_ERR_ARG, "smem_links must be 0, 1, 2 or 3");
     if (smem_links >= 2 && rhs_tile != 1) return set_error(PLQ_ERR_ARG, "smem_links 2 and 3 need rhs_tile 1");
+    if (smem_links == 1 && rhs_tile == 4) return set_error(PLQ_ERR_ARG, "smem_links 1 needs rhs_tile 1 or 2");
     PLQ_CUDA(cudaSetDevice(c->device));
     if (index_mode == 1) PLQ_TRY(ensure_nbr_tables(c));
     c->tune[prec][nrhs].block = block;

@@ -155,7 +155,7 @@ def test_multi_rhs_shared_staging_ragged(sm, prec, reals, nrhs, block):
 def test_set_launch_rejects_bad_staging():
     dims = (4, 4, 2, 4)
     with Context(dims) as ctx:
-        for sm, tile in ((4, 1), (-1, 1), (2, 2), (3, 4)):
+        for sm, tile in ((4, 1), (-1, 1), (2, 2), (3, 4), (1, 4)):
             with pytest.raises(PLQError) as e:
                 ctx.set_launch(F32, 4, 64, 0, tile, 0, sm)
             assert e.value.status == plq.PLQ_ERR_ARG

@@ -209,10 +209,19 @@ PLQ_API plq_status plq_hopping_eo(plq_ctx *ctx, int out_parity, void *out, const
 
 /* Same operation on HOST buffers (packed layout, pinned or pageable): the
  * input half field is copied to the device, the operator applied and the
- * result copied back; the stream is synchronised before return.  Uses a
- * library-owned device staging area. */
+ * result copied back, pipelined over time slabs (plq_host_slabs) so that
+ * copies in, compute and copies out overlap -- the communication/computation
+ * overlap of Sec. 2.2 applied to the host link; the stream is synchronised
+ * before return.  Uses a library-owned device staging area. */
 PLQ_API plq_status plq_hopping_eo_host(plq_ctx *ctx, int out_parity, void *out_host, const void *in_host, int prec, int nrhs,
                                void *stream);
+
+/* Time slabs of the plq_hopping_eo_host pipeline for time extent T (even, >= 2):
+ * writes the slab boundaries bounds[0] = 0 < bounds[1] < ... < bounds[K] = T
+ * (caller-owned, room for 65 ints) and returns K <= 64, or 0 on bad arguments.
+ * Slabs grow 1, 1, 2, 4, ... time slices (each below T/8) from both ends with
+ * slabs of T/8 slices between them.  Host only; no device work. */
+PLQ_API int plq_host_slabs(int T, int *bounds);
 
 /* Wilson operator on the full lattice: out = M in = in - kappa * H in.
  * `in` and `out` are packed full fields (even half then odd half) of

@@ -400,6 +400,14 @@ plq_status enqueue_host_pipeline(plq_ctx *c, int out_parity, char *hout, const c
 
 extern "C" {
 
+int plq_host_slabs(int T, int *bounds) {
+    if (T < 2 || (T & 1) || !bounds) return 0;
+    int b[kMaxHostSlabs + 1];
+    const int K = host_slab_bounds(T, b);
+    for (int k = 0; k <= K; ++k) bounds[k] = b[k];
+    return K;
+}
+
 plq_status plq_hopping_eo_host(plq_ctx *c, int out_parity, void *out_host, const void *in_host, int prec, int nrhs,
                                void *stream) {
     PLQ_TRY(check_ctx(c));

@@ -131,6 +131,7 @@ SIGNATURES = {
     "plq_schur_apply_noalloc": (_c_int, [_vp, _vp, _vp, _c_double, _c_int, _c_int, _vp]),
     "plq_autotune": (_c_int, [_vp, _c_int, _c_int, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
     "plq_set_launch": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int, _c_int]),
+    "plq_host_slabs": (_c_int, [_c_int, ctypes.POINTER(_c_int)]),
 }
 
 _lib = None

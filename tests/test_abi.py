@@ -102,3 +102,20 @@ def test_binding_argument_counts_match_header():
         args = args.strip()
         n = 0 if args in ("", "void") else args.count(",") + 1
         assert len(plq.SIGNATURES[name][1]) == n, name
+
+
+def test_host_slab_schedule(lib):
+    """The time slabs of the host pipeline: they tile [0, T), each holds at least one
+    time slice (so slab k's t +- 1 neighbours lie in slabs k - 1 .. k + 1), none holds
+    more than max(1, T/8), the first and last hold one slice, and there are at most 64."""
+    b = (ctypes.c_int * 65)()
+    for T in range(2, 4098, 2):
+        K = lib.plq_host_slabs(T, b)
+        bounds = list(b[:K + 1])
+        sizes = [bounds[k + 1] - bounds[k] for k in range(K)]
+        assert 1 <= K <= 64 and bounds[0] == 0 and bounds[-1] == T, T
+        assert min(sizes) >= 1 and max(sizes) <= max(1, T // 8), (T, sizes)
+        assert sizes[0] == 1 and sizes[-1] == 1, (T, sizes)
+    K = lib.plq_host_slabs(64, b)
+    assert [b[k + 1] - b[k] for k in range(K)] == [1, 1, 2, 4, 8, 8, 8, 8, 8, 8, 4, 2, 1, 1]
+    assert lib.plq_host_slabs(7, b) == 0 and lib.plq_host_slabs(0, b) == 0 and lib.plq_host_slabs(8, None) == 0

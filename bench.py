@@ -12,6 +12,12 @@ Also reported on the same JSON line:
   * every storage format of the operator (FP64/FP32/FP16, 18/12-real links),
   * the solver comparison: FP64 CG vs mixed FP32/FP16-inner CG with FP64
     reliable updates to a true residual of 1e-10 on 24^3 x 48 (kappa 0.120),
+  * batch: 16 uneven solves (8^3x16 / 16^3x32 / 24^3x48, kappa in [0.110,
+    0.124]) in one persistent launch of the batched mixed CG, against the same
+    systems solved one after the other by mixed CG and by plain FP64 CG,
+  * propagator: 48^3x96 (kappa 0.121) with 12 point sources: the multi-RHS
+    operator, the 12-RHS mixed CG, single-RHS mixed solves and plain FP64 CG
+    on a sample of the sources,
   * e2e: the same operator through plq_hopping_eo_host with pinned host
     buffers (host->device and device->host copies inside the timed region),
   * cpu_baseline: the FP64 C oracle (OpenMP site loop) on the host cores.
@@ -177,6 +183,46 @@ def output_sites(dims, parity):
     return lex[((t + x + y + z) % 2) == parity].astype(np.int64)
 
 
+def host_info(threads_used=None):
+    """The host the CPU oracle runs on: CPU model, logical CPUs, the CPUs this
+    process may run on (affinity / cgroup) and the OpenMP thread setting."""
+    info = {"machine": os.uname().machine, "nproc": os.cpu_count()}
+    try:
+        info["affinity_cpus"] = len(os.sched_getaffinity(0))
+    except Exception:
+        info["affinity_cpus"] = None
+    model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    info["cpu_model"] = model
+    try:
+        with open("/sys/fs/cgroup/cpu.max") as f:
+            info["cgroup_cpu_max"] = f.read().strip()
+    except Exception:
+        info["cgroup_cpu_max"] = None
+    info["omp_num_threads_env"] = os.environ.get("OMP_NUM_THREADS")
+    if threads_used is not None:
+        lim = info["affinity_cpus"] or info["nproc"]
+        info["threads_used"] = threads_used
+        info["all_available_cpus_used"] = bool(lim is not None and threads_used >= lim)
+    return info
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -201,7 +247,8 @@ def run_reference(args, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "hopping half-apply 32^3x64 (sampled 1/8 of output sites)", "lattice": "32^3x64"},
-        "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": gflops, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": desc,
+                         "host": host_info(cores)},
         "e2e": {"value": gflops, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -377,8 +424,9 @@ def cg_section(torch, local_rank, quick):
     return out
 
 
-def propagator_section(torch, local_rank, quick):
-    """12 point sources (spin x colour at the origin): multi-RHS operator and batched mixed CG."""
+def propagator_section(torch, local_rank, quick, fp64_rhs=4):
+    """12 point sources (spin x colour at the origin): multi-RHS operator, batched mixed CG
+    and, as the comparator, plain FP64 CG on the first `fp64_rhs` sources."""
     from paper_1405_0700_gb300 import DF64, F16, F32, F64, Context
 
     dims = (96, 48, 48, 48) if not quick else (16, 8, 8, 8)
@@ -491,6 +539,33 @@ def propagator_section(torch, local_rank, quick):
             "solves": len(singles), "seconds_per_rhs": float(np.mean([s_[0] for s_ in singles])),
             "iterations": [s_[1] for s_ in singles], "max_true_rel_residual": max(s_[2] for s_ in singles)}
         out["speedup_batched_vs_single_per_rhs"] = out["single_rhs_cg_mixed_f32"]["seconds_per_rhs"] / (el / n)
+        # plain FP64 CG (FP64 storage and arithmetic throughout) on the first
+        # n_fp64 point sources, one at a time: the comparator of the mixed solves
+        n64 = max(1, min(n, fp64_rhs if not quick else 1))
+        f64 = []
+        for r in range(n64):
+            bs = torch.zeros(V * 24, dtype=torch.float64, device=f"cuda:{local_rank}")
+            bs[2 * r] = 1.0
+            b1 = ctx.empty_full(F64)
+            ctx.pack_spinor(b1, bs, F64)
+            x1 = ctx.empty_full(F64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = ctx.cg_solve(x1, b1, kappa, tol=1e-10, inner_prec=F64, maxit=3000, raise_on_error=False)
+            torch.cuda.synchronize()
+            f64.append((time.perf_counter() - t0, info.iterations, info.true_rel_residual, info.status))
+            log(f"[bench] FP64 CG point source {r}: {f64[-1][0]:.2f}s it={info.iterations} "
+                f"res={info.true_rel_residual:.2e}")
+            del bs, b1, x1
+        per64 = float(np.mean([v[0] for v in f64]))
+        out["fp64_cg"] = {
+            "solves": len(f64), "sample": f"point sources 0..{len(f64) - 1} of {n}, one solve each",
+            "seconds_per_rhs": per64, "iterations": [v[1] for v in f64],
+            "max_true_rel_residual": max(v[2] for v in f64), "status": [v[3] for v in f64]}
+        bm = out["batched_cg_mixed_f32"]
+        out["speedup_vs_fp64"] = per64 / bm["seconds_per_rhs"]
+        out["all_converged_1e-10"] = bool(
+            bm["max_true_rel_residual"] <= 1e-10 and out["fp64_cg"]["max_true_rel_residual"] <= 1e-10)
     return out
 
 
@@ -616,25 +691,42 @@ def batch_section(torch, local_rank, quick):
     t_batch = time.perf_counter() - t0
     for ctx in ctxs:
         ctx.autotune(F32, 1)
-    seq = []
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for ctx, x, b, k in zip(ctxs, xs, bs, kappas):
-        seq.append(ctx.cg_solve(x, b, k, inner_prec=F32, raise_on_error=False))
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
+
+    def sequential(inner):
+        # every system once untimed (graphs instantiated, caches warm), then timed
+        for ctx, x, b, k in zip(ctxs, xs, bs, kappas):
+            ctx.cg_solve(x, b, k, inner_prec=inner, raise_on_error=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = [ctx.cg_solve(x, b, k, inner_prec=inner, raise_on_error=False)
+               for ctx, x, b, k in zip(ctxs, xs, bs, kappas)]
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+    t_seq, seq = sequential(F32)
+    t_seq64, seq64 = sequential(F64)
+    res_all = ([i.true_rel_residual for i in infos] + [i.true_rel_residual for i in seq] +
+               [i.true_rel_residual for i in seq64])
     out = {"solves": len(specs), "lattices": [("x".join(map(str, sp["dims"][1:])) + "x" + str(sp["dims"][0]))
                                               for sp in specs],
-           "kappas": kappas, "persistent": {"seconds": t_batch, **binfo,
-                                            "iterations": [i.iterations for i in infos],
-                                            "true_rel_residual": [i.true_rel_residual for i in infos],
-                                            "status": [i.status for i in infos]},
-           "sequential": {"seconds": t_seq, "iterations": [i.iterations for i in seq],
-                          "true_rel_residual": [i.true_rel_residual for i in seq]},
-           "speedup_persistent_vs_sequential": t_seq / t_batch}
+           "kappas": kappas, "tol": 1e-10,
+           "persistent": {"seconds": t_batch, **binfo,
+                          "iterations": [i.iterations for i in infos],
+                          "true_rel_residual": [i.true_rel_residual for i in infos],
+                          "status": [i.status for i in infos]},
+           "sequential_mixed": {"seconds": t_seq, "inner": "f32 storage, FP64 reliable updates",
+                                "iterations": [i.iterations for i in seq],
+                                "true_rel_residual": [i.true_rel_residual for i in seq]},
+           "sequential_fp64": {"seconds": t_seq64, "inner": "plain FP64 CG",
+                               "iterations": [i.iterations for i in seq64],
+                               "true_rel_residual": [i.true_rel_residual for i in seq64]},
+           "speedup_persistent_vs_sequential": t_seq / t_batch,
+           "speedup_vs_fp64": t_seq64 / t_batch,
+           "all_converged_1e-10": bool(max(res_all) <= 1e-10)}
     for c in ctxs:
         c.close()
-    log(f"[bench] batch of {len(specs)}: persistent {t_batch:.3f}s ({binfo}) vs sequential {t_seq:.3f}s")
+    log(f"[bench] batch of {len(specs)}: persistent {t_batch:.3f}s ({binfo}) vs sequential mixed {t_seq:.3f}s, "
+        f"sequential FP64 {t_seq64:.3f}s")
     return out
 
 
@@ -646,6 +738,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 16-solve persistent batch section")
+    ap.add_argument("--no-propagator", action="store_true", help="skip the 48^3x96 12-source propagator section")
+    ap.add_argument("--fp64-rhs", type=int, default=4,
+                    help="point sources solved by plain FP64 CG as the propagator section's comparator")
     ap.add_argument("--quick", action="store_true", help="small lattices (smoke use only)")
     ap.add_argument("--source-hash", action="store_true", help="print the hash of the headline kernel's sources")
     ap.add_argument("--workload", default="hop", choices=["hop", "propagator", "operator", "eigcg", "batch", "stream"],
@@ -694,7 +790,7 @@ def main():
             print(json.dumps({"workload": "eigcg", **res}), flush=True)
         return
     if args.workload == "propagator":
-        res = propagator_section(torch, local_rank, args.quick)
+        res = propagator_section(torch, local_rank, args.quick, args.fp64_rhs)
         if rank == 0:
             print(json.dumps({"workload": "propagator", **res}), flush=True)
         return
@@ -779,6 +875,14 @@ def main():
     cg = None
     if not args.no_cg:
         cg = cg_section(torch, local_rank, args.quick)
+    batch = None
+    if not args.no_batch:
+        batch = batch_section(torch, local_rank, args.quick)
+        torch.cuda.empty_cache()
+    prop = None
+    if not args.no_propagator:
+        prop = propagator_section(torch, local_rank, args.quick, args.fp64_rhs)
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -790,7 +894,7 @@ def main():
 
         C.threads(cores)
         cpu = {"value": FLOP_PER_SITE * len(sites) / med / 1e9, "unit": "GFLOP/s", "cores": cores,
-               "kind": "oracle",
+               "kind": "oracle", "host": host_info(cores),
                "sample": f"C oracle (FP64 Eq. (1) site loop, OpenMP) over all {len(sites)} even output sites of the "
                          f"same 32^3x64 half-application, median of {reps} repetitions ({el:.1f}s)",
                "single_thread": {"value": FLOP_PER_SITE * len(sites) / med1 / 1e9, "unit": "GFLOP/s", "cores": 1,
@@ -824,6 +928,8 @@ def main():
             "gbs_no_reuse_convention": head["gbs_no_reuse_convention"],
             "variants": variants,
             "cg": cg,
+            "batch": batch,
+            "propagator": prop,
             "theta_two_pass": theta,
             "link_spinor_stream": stream,
             "e2e": e2e,

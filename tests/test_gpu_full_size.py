@@ -99,3 +99,33 @@ def test_batched_benchmark_lattice_sizes():
         assert res <= 1e-10, (sp["dims"], res, infos[k].as_dict())
     for c in ctxs:
         c.close()
+
+
+def test_batched_sixteen_uneven_systems():
+    """The whole batch workload: 16 systems (lattices cycling 8^3x16 / 16^3x32 / 24^3x48,
+    per-system seeds and kappas in [0.110, 0.124]) in one persistent launch of the mixed
+    FP32-inner CG; every returned x is checked with the C oracle's Wilson operator."""
+    specs = S.batch_solve_specs(n=16)
+    ctxs, xs, bs, Us, srcs = [], [], [], [], []
+    for sp in specs:
+        U, b = S.gauge_and_spinor(sp["dims"], sp["eps"], sp["seed"])
+        ctx = Context(sp["dims"])
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        ctxs.append(ctx)
+        bs.append(ctx.to_device(b, F64))
+        xs.append(ctx.empty_full(F64))
+        Us.append(U)
+        srcs.append(b)
+    infos, binfo = P.cg_solve_batched(ctxs, xs, bs, [sp["kappa"] for sp in specs], inner_prec=F32)
+    assert binfo["launches"] == 1
+    iters = set()
+    for k, sp in enumerate(specs):
+        xk = ctxs[k].to_host(xs[k], F64)
+        res = float(np.linalg.norm(srcs[k] - C.wilson(Us[k], xk, sp["kappa"])) / np.linalg.norm(srcs[k]))
+        assert res <= 1e-10, (k, sp["dims"], res, infos[k].as_dict())
+        assert abs(infos[k].true_rel_residual - res) < 1e-11, (k, infos[k].true_rel_residual, res)
+        iters.add(infos[k].iterations)
+    assert len(iters) > 1  # uneven systems: the batch really retires systems at different times
+    for c in ctxs:
+        c.close()

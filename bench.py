@@ -683,6 +683,9 @@ def batch_section(torch, local_rank, quick):
         bs.append(ctx.to_device(b, F64))
         xs.append(ctx.empty_full(F64))
     kappas = [sp["kappa"] for sp in specs]
+    # the launch shape (threads per block, resident blocks per SM) chosen by the library's tuner
+    tuned = P.autotune_batched(ctxs, xs, bs, kappas, inner_prec=F32,
+                               cache_path=os.environ.get("PLQ_TUNE_CACHE"))
     P.cg_solve_batched(ctxs, xs, bs, kappas, inner_prec=F32, raise_on_error=False)  # warm
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -710,7 +713,7 @@ def batch_section(torch, local_rank, quick):
     out = {"solves": len(specs), "lattices": [("x".join(map(str, sp["dims"][1:])) + "x" + str(sp["dims"][0]))
                                               for sp in specs],
            "kappas": kappas, "tol": 1e-10,
-           "persistent": {"seconds": t_batch, **binfo,
+           "persistent": {"seconds": t_batch, **binfo, "tuned_launch": tuned,
                           "iterations": [i.iterations for i in infos],
                           "true_rel_residual": [i.true_rel_residual for i in infos],
                           "status": [i.status for i in infos]},

@@ -151,27 +151,54 @@ typedef struct {
 } plq_solve_info;
 
 /* Message of the last error in this thread ("" if none).  The pointer stays
- * valid until the next failing call in the same thread. */
+ * valid until the next failing call in the same thread.
+ * Defined by: paper silent (error reporting of this library). */
 PLQ_API const char *plq_last_error(void);
 
-/* Library version, major*10000 + minor*100 + patch. */
+/* Library version, major*10000 + minor*100 + patch.
+ * Defined by: paper silent. */
 PLQ_API int plq_version(void);
 
 /* Create a context for a lattice on CUDA device `device` (made current for
  * the calling thread).  dims as described above; t_bc is -1 (antiperiodic
  * time, the default physics) or +1.  Returns PLQ_ERR_ARG for odd or < 2
  * extents, volumes above 2^30 sites, or |t_bc| != 1.  *ctx receives the
- * handle; release it with plq_finalize. */
+ * handle; release it with plq_finalize.
+ * Defined by: Sec. 2, Eq. (1) (a four-dimensional lattice, directions
+ * mu = 0..3, nearest-neighbour hops).  Paper silent on which mu is time, on
+ * the boundary conditions and on the even-odd split; the readings taken are
+ * those stated at the top of this header. */
 PLQ_API plq_status plq_init(plq_ctx **ctx, const int dims[4], int t_bc, int device);
 
-/* Free every device and host resource of the context.  NULL is accepted. */
+/* Free every device and host resource of the context.  NULL is accepted.
+ * Defined by: paper silent (resource management of this library). */
 PLQ_API plq_status plq_finalize(plq_ctx *ctx);
 
-/* Number of sites of one parity, Vh. */
+/* Defined by: paper silent (failure detection of this library's kernels).
+ *
+ * Longest time a wait inside a kernel of this context may take (the
+ * row-streamed hopping kernel waits for its shared-memory copies) before it
+ * gives up: the kernel then records PLQ_ERR_TIMEOUT in the context's device
+ * status word, leaves its output incomplete and returns (default about 5 s).
+ * Host only; takes effect for the launches that follow. */
+PLQ_API plq_status plq_set_wait_limit(plq_ctx *ctx, double seconds);
+
+/* Defined by: paper silent (failure detection of this library's kernels).
+ *
+ * Reads the context's device status word (synchronising the device): PLQ_OK,
+ * or the error a kernel recorded (PLQ_ERR_TIMEOUT: a bounded wait gave up),
+ * which is then also the return value.  clear != 0 resets the word. */
+PLQ_API plq_status plq_device_status(plq_ctx *ctx, int clear);
+
+/* Number of sites of one parity, Vh.
+ * Defined by: paper silent (the even-odd split is a reading: sites of one
+ * parity only hop to sites of the other, Eq. (1)). */
 PLQ_API long plq_half_volume(const plq_ctx *ctx);
 
 /* Bytes of one packed half field of precision `prec` holding `nrhs`
- * right-hand sides (0 on bad arguments). */
+ * right-hand sides (0 on bad arguments).
+ * Defined by: paper silent on storage (Sec. 4 only mentions data-ordering
+ * strategies); the layouts are those described at the top of this header. */
 PLQ_API size_t plq_field_bytes(const plq_ctx *ctx, int prec, int nrhs);
 
 /* Pack the gauge field into the library-owned copy of precision `prec`
@@ -193,10 +220,13 @@ PLQ_API plq_status plq_gauge_upload(plq_ctx *ctx, const double *U, int is_device
  *   out  device, 2 * plq_field_bytes(prec, nrhs) bytes: the even half field
  *        then the odd half field, right-hand sides interleaved as described
  *        above.
- * Conversion to FP32 / FP16 rounds to nearest; FP16 stores component/norm. */
+ * Conversion to FP32 / FP16 rounds to nearest; FP16 stores component/norm.
+ * Defined by: the spinor phi(x) of Eq. (1) (4 spin x 3 colour complex
+ * components per site); paper silent on layouts and reduced precisions. */
 PLQ_API plq_status plq_pack_spinor(plq_ctx *ctx, void *out, const double *in, int prec, int nrhs, void *stream);
 
-/* Packed full field of precision `prec` -> `nrhs` canonical FP64 fields. */
+/* Packed full field of precision `prec` -> `nrhs` canonical FP64 fields.
+ * Defined by: the inverse of plq_pack_spinor (paper silent on layouts). */
 PLQ_API plq_status plq_unpack_spinor(plq_ctx *ctx, double *out, const void *in, int prec, int nrhs, void *stream);
 
 /* Half-lattice hopping operator (Eq. (1) restricted to one output parity):
@@ -216,7 +246,9 @@ PLQ_API plq_status plq_hopping_eo(plq_ctx *ctx, int out_parity, void *out, const
 PLQ_API plq_status plq_hopping_eo_host(plq_ctx *ctx, int out_parity, void *out_host, const void *in_host, int prec, int nrhs,
                                void *stream);
 
-/* Time slabs of the plq_hopping_eo_host pipeline for time extent T (even, >= 2):
+/* Time slabs of the plq_hopping_eo_host pipeline (Sec. 2.2: the lattice split
+ * so that transfers of one part overlap computation on another) for time
+ * extent T (even, >= 2):
  * writes the slab boundaries bounds[0] = 0 < bounds[1] < ... < bounds[K] = T
  * (caller-owned, room for 65 ints) and returns K <= 64, or 0 on bad arguments.
  * Slabs grow 1, 1, 2, 4, ... time slices (each below T/8) from both ends with
@@ -225,7 +257,10 @@ PLQ_API int plq_host_slabs(int T, int *bounds);
 
 /* Wilson operator on the full lattice: out = M in = in - kappa * H in.
  * `in` and `out` are packed full fields (even half then odd half) of
- * precision `prec`, nrhs = 1; they must not overlap. */
+ * precision `prec`, nrhs = 1; they must not overlap.
+ * Defined by: H is Eq. (1) of Sec. 2 (the hopping part of the Wilson-Dirac
+ * operator); the normalisation M = 1 - kappa H (hopping parameter kappa, no
+ * factor 1/2 in the projectors) is a reading, the paper being silent on it. */
 PLQ_API plq_status plq_wilson_apply(plq_ctx *ctx, void *out, const void *in, double kappa, int prec, void *stream);
 
 /* Twisted-mass Wilson operator (the fermions of the paper's Sec. 3 EigCG
@@ -240,11 +275,19 @@ PLQ_API plq_status plq_twisted_apply(plq_ctx *ctx, void *out, const void *in, do
 
 /* Even-odd Schur operator on even half fields: out = Mhat in =
  * in - kappa^2 H_eo H_oe in (dagger != 0: Mhat^dagger = gamma5 Mhat gamma5).
- * `tmp` is a caller-owned odd half field of the same precision. */
+ * `tmp` is a caller-owned odd half field of the same precision.
+ * Defined by: two half-lattice applications of Eq. (1) (Sec. 2); the even-odd
+ * preconditioning itself is a reading (paper silent). */
 PLQ_API plq_status plq_schur_apply(plq_ctx *ctx, void *out, const void *in, void *tmp, double kappa, int dagger, int prec,
                            void *stream);
 
-/* Solve M x = b by conjugate gradients on the even-odd preconditioned normal
+/* Defined by: Sec. 4 states that the library holds "a few associated
+ * solvers" for the Wilson-Dirac operator of Eq. (1) without naming them
+ * (paper silent on the algorithms); CG on the even-odd normal equations and
+ * BiCGstab are the readings taken, mixed precision with reliable updates
+ * follows Clark et al. (2010).
+ *
+ * Solve M x = b by conjugate gradients on the even-odd preconditioned normal
  * equations Mhat^dagger Mhat x_e = Mhat^dagger bhat, bhat = b_e + kappa H_eo b_o,
  * then x_o = b_o + kappa H_oe x_e.  x and b are packed full FP64 fields.
  * inner_prec PLQ_F32/PLQ_F16 runs the Krylov iteration at that precision with
@@ -255,11 +298,17 @@ PLQ_API plq_status plq_cg_solve(plq_ctx *ctx, void *x, const void *b, double kap
                         plq_solve_info *info, void *stream);
 
 /* Same system solved by BiCGstab on Mhat x_e = bhat (no normal equations).
- * Returns PLQ_ERR_BREAKDOWN when rho or omega vanish. */
+ * Returns PLQ_ERR_BREAKDOWN when rho or omega vanish.
+ * Defined by: paper silent on the algorithm (see plq_cg_solve); BiCGstab of
+ * van der Vorst (1992). */
 PLQ_API plq_status plq_bicgstab_solve(plq_ctx *ctx, void *x, const void *b, double kappa, const plq_solver_params *params,
                               plq_solve_info *info, void *stream);
 
-/* Several right-hand sides at once: x and b are packed full FP64 fields
+/* Defined by: the solvers above (paper silent on the algorithms) with the
+ * operator applied to several vectors per link load, Sec. 2.3's one SU(3)
+ * matrix times two vectors widened to up to 12.
+ *
+ * Several right-hand sides at once: x and b are packed full FP64 fields
  * holding `nrhs` (1..PLQ_MAX_RHS) interleaved right-hand sides (as produced
  * by plq_pack_spinor with that nrhs); `infos` points to nrhs reports.  Every
  * operator application of the solve loads each link once for all of them
@@ -300,6 +349,13 @@ typedef struct plq_eigcg plq_eigcg;
 PLQ_API plq_status plq_eigcg_create(plq_ctx *ctx, int nev, int m, int max_vectors, plq_eigcg **out);
 PLQ_API plq_status plq_eigcg_destroy(plq_eigcg *eig);
 PLQ_API int plq_eigcg_vectors(const plq_eigcg *eig);
+/* The projected matrix H = U^H A U of the deflation basis (Sec. 3: the
+ * Rayleigh-Ritz matrix whose eigenvalues approximate the lowest eigenvalues
+ * of A): with k = plq_eigcg_vectors(eig) basis vectors, writes H[i][j] as
+ * (re, im) doubles at H[2*(i*ld + j)] for i, j < k (host memory, caller-owned,
+ * ld >= k) and returns k; with H == NULL only returns k.  -1 on a NULL handle
+ * or ld < k.  Host copy only; no device work. */
+PLQ_API int plq_eigcg_projected_matrix(const plq_eigcg *eig, double *H, int ld);
 PLQ_API plq_status plq_eigcg_solve(plq_eigcg *eig, void *x, const void *b, double kappa,
                                    const plq_solver_params *params, int accumulate, plq_solve_info *info,
                                    void *stream);
@@ -311,9 +367,24 @@ typedef struct {
     int graph_captured;  /* 1 if the launch ran as a captured CUDA graph       */
     int launches;        /* kernel launches of the solve (1 on success)        */
     double seconds;      /* time of the persistent kernel                      */
+    int blocks_per_sm;   /* resident blocks per SM launched                     */
+    int graph_reused;    /* 1 if the instantiated graph of an earlier call with
+                            the same launch was replayed                        */
 } plq_batch_info;
 
-/* Batched CG: n (1..64) independent systems M_k x_k = b_k -- different
+/* Defined by: paper silent (the CG of plq_cg_solve, whose algorithm the
+ * paper does not name, applied to many independent systems at once).
+ *
+ * The descriptor scratch, the internal stream and the instantiated CUDA graph
+ * of the launch are kept in ctxs[0] (freed by its plq_finalize): a later call
+ * with ctxs[0] first and the same launch shape, number of systems and
+ * parameters replays that graph (plq_batch_info.graph_reused) after
+ * rewriting the descriptors, so it may solve other systems, sources or
+ * kappas.  The launch shape (threads per block, resident blocks per SM) is
+ * the one set on ctxs[0] by plq_set_batched_launch or plq_autotune_batched,
+ * else 128 threads and all blocks that fit.
+ *
+ * Batched CG: n (1..64) independent systems M_k x_k = b_k -- different
  * lattices (one context each, same device), kappas and iteration counts --
  * solved by ONE persistent cooperative kernel launch, captured in a CUDA
  * graph.  Each system runs the algorithm of plq_cg_solve (even-odd normal
@@ -333,18 +404,45 @@ PLQ_API plq_status plq_cg_solve_batched(plq_ctx **ctxs, int n, void **x, const v
                                         const plq_solver_params *params, plq_solve_info *infos,
                                         plq_batch_info *binfo, void *stream);
 
+/* Defined by: paper silent (launch parameters of plq_cg_solve_batched).
+ *
+ * Launch shape of the persistent batched kernel for batches whose first
+ * context is `ctx`: block = threads per block, 64, 128, 192 or 256 (0: 128),
+ * compiled with the register budget of 512 resident threads per SM (192:
+ * 384 threads, 168 registers), and blocks_per_sm = resident blocks per SM to
+ * launch (0: as many as fit; values above that are clamped). */
+PLQ_API plq_status plq_set_batched_launch(plq_ctx *ctx, int block, int blocks_per_sm);
+
+/* Defined by: paper silent (tuner of plq_cg_solve_batched's launch).
+ *
+ * Times plq_cg_solve_batched on the given systems (same arguments; x is
+ * overwritten by the solves) for every block size of plq_set_batched_launch
+ * with all resident blocks per SM and with one fewer, each solved twice and
+ * timed on the second call (which replays the captured graph), and keeps the
+ * fastest kernel time in ctxs[0].  cache_path (NULL: the PLQ_TUNE_CACHE
+ * environment variable, if set) names the text file of plq_autotune: a line
+ * keyed by GPU name, inner precision, link format, number of systems and
+ * their lattices skips the timing; a miss appends the result.  best (may be
+ * NULL) receives the launch report of the chosen shape (from the cache:
+ * block, blocks_per_sm and seconds only).  Synchronises the device. */
+PLQ_API plq_status plq_autotune_batched(plq_ctx **ctxs, int n, void **x, const void **b, const double *kappa,
+                                        const plq_solver_params *params, const char *cache_path,
+                                        plq_batch_info *best);
+
 /* Allocation-free Schur operator.  No counterpart in the paper: this is a
  * service to callers that cannot allocate device memory at the moment they
- * apply the operator -- code running while a CUDA graph is being captured
- * (cudaMalloc is not permitted during capture), applications that give all
- * device memory to their own pool and forbid other allocations, and real-time
- * loops that must not take the allocator's locks.  It computes the same
- * result as plq_schur_apply (out = Mhat in, or Mhat^dagger in when dagger !=
- * 0) but keeps the odd-parity intermediate H_oe in in a fixed device array of
- * PLQ_NOALLOC_SCRATCH_BYTES bytes compiled into the library, so the call
- * itself allocates nothing: no cudaMalloc, cudaFree or allocating library
- * routine.  (The context, its gauge copy and the in/out fields are set up
- * beforehand, as for every other call.)
+ * apply the operator -- applications that hand all device memory to their
+ * own pool or allocator and forbid anyone else from calling cudaMalloc,
+ * real-time or latency-critical loops that must not take the allocator's
+ * locks or wait for it, and callers that run under a fixed device-memory
+ * budget agreed at start-up.  It computes the same result as plq_schur_apply
+ * (out = Mhat in, or Mhat^dagger in when dagger != 0), in the same launch
+ * configuration (plq_autotune / plq_set_launch), but keeps the odd-parity
+ * intermediate H_oe in in a fixed device array of PLQ_NOALLOC_SCRATCH_BYTES
+ * bytes compiled into the library, so the call itself allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library routine.  (The context, its
+ * gauge copy and the in/out fields are set up beforehand, as for every other
+ * call.)
  *   in, out   caller-owned even half fields of precision `prec`, distinct.
  *   Limits    PLQ_ERR_ARG when one odd half field of `prec` is larger than
  *             PLQ_NOALLOC_SCRATCH_BYTES (8 MiB: Vh up to 43,690 sites in FP64,
@@ -352,11 +450,15 @@ PLQ_API plq_status plq_cg_solve_batched(plq_ctx **ctxs, int n, void **x, const v
  * The array exists once per GPU that loads the library and stays allocated
  * until the process exits.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress, with that device current) and caches
- * it; make that first call before any stream capture.  Every call on a device
- * shares the one array: calls whose kernels overlap on the GPU (different
- * streams, or different contexts on the same device) race on it and must be
- * serialised by the caller.  The array keeps the last call's contents; each
- * call overwrites all of the part it reads before reading it. */
+ * it; make that first call before any stream capture.  A cudaDeviceReset
+ * destroys the module instance the cached address points into, together with
+ * every context created before it; the next call after a reset sees that the
+ * cached address no longer belongs to the device and looks it up again.
+ * Every call on a device shares the one array: calls whose kernels overlap
+ * on the GPU (different streams, or different contexts on the same device)
+ * race on it and must be serialised by the caller.  The array keeps the last
+ * call's contents; each call overwrites all of the part it reads before
+ * reading it. */
 #define PLQ_NOALLOC_SCRATCH_BYTES (8u << 20)
 PLQ_API plq_status plq_schur_apply_noalloc(plq_ctx *ctx, void *out, const void *in, double kappa, int dagger,
                                            int prec, void *stream);
@@ -369,7 +471,11 @@ typedef struct {
     int z_chunk;          /* site order: 0 = time slowest; z > 0 = z-chunks of z planes    */
     int smem_links;       /* nrhs > 1: 0 none; 1 links of a block of sites staged in shared
                              memory; 2 / 3 the same plus the neighbour spinors of the next
-                             1 / 2 directions copied ahead into per-thread shared slots   */
+                             1 / 2 directions copied ahead into per-thread shared slots;
+                             any nrhs (FP32/FP16): 4 row-streamed kernel, whole rows of
+                             neighbour spinors and links copied into a ring of shared-
+                             memory slots by bulk (TMA) copies; sites_per_thread is then
+                             the number of slots (0: as many as fit)                   */
     double us_per_launch; /* measured time of one half-lattice application                 */
     int from_cache;       /* 1 if the choice came from the cache file                      */
     int candidates;       /* configurations timed                                          */
@@ -401,11 +507,16 @@ typedef struct {
  * `res` may be NULL. */
 PLQ_API plq_status plq_autotune(plq_ctx *ctx, int prec, int nrhs, const char *cache_path, plq_tune_result *res);
 
-/* Set the hopping launch of (prec, nrhs) by hand: block = threads per block
+/* Defined by: the launch parameters that plq_autotune sweeps (index mode:
+ * the pointer arrays of Sec. 2.2; right-hand-side tiles: Sec. 2.3).
+ *
+ * Set the hopping launch of (prec, nrhs) by hand: block = threads per block
  * (0 = library default, else a multiple of 32 up to 1024; a block the kernel
  * cannot launch makes the operator calls return PLQ_ERR_ARG), index_mode 0 or 1,
  * rhs_tile 1, 2 or 4 (dividing nrhs), z_chunk 0 or a divisor of Lz and
- * smem_links 0..3 (nrhs > 1, FP32/FP16; with 1, rhs_tile 1 or 2; with 2 or 3,
+ * smem_links 0..4 (1..3: nrhs > 1, FP32/FP16; 4: FP32/FP16, needs nrhs x Lx/2
+ * <= 512 and 16-byte row runs, else the operator calls return PLQ_ERR_ARG;
+ * with 1, rhs_tile 1 or 2; with 2, 3 or 4,
  * rhs_tile 1) and sites_per_thread 0..64, as above. */
 PLQ_API plq_status plq_set_launch(plq_ctx *ctx, int prec, int nrhs, int block, int index_mode, int rhs_tile,
                                   int z_chunk, int smem_links, int sites_per_thread);
@@ -438,7 +549,8 @@ PLQ_API plq_status plq_hopping_eo_theta(plq_ctx *ctx, int out_parity, void *out,
 PLQ_API plq_status plq_link_spinor_stream(int mode, long long nsites, const void *U, const void *phi, void *psi,
                                           const int *index, const void *const *pointers, int prec, void *stream);
 
-/* Roofline calibration (a measurement helper; the paper has no counterpart):
+/* Roofline calibration (a measurement helper; paper silent, it has no
+ * counterpart):
  * the sustained FMA throughput of the CUDA cores of `device` in FP64
  * (prec = PLQ_F64) or FP32 (PLQ_F32), in flop/s (an FMA counts 2), measured
  * with independent FMA chains in every thread of a full-GPU grid.  Allocates

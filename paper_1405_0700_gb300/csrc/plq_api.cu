@@ -1,6 +1,7 @@
 // C ABI of libplq: context, errors, gauge upload, layout conversion and the
 // operator entry points (hopping, Wilson, Schur).  Solvers live in
 // plq_solvers.cu.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -142,12 +143,17 @@ plq_status plq_init(plq_ctx **out, const int dims[4], int t_bc, int device) {
     PLQ_CUDA(cudaSetDevice(device));
     plq_ctx *c = new (std::nothrow) plq_ctx();
     if (!c) return set_error(PLQ_ERR_NOMEM, "host allocation");
-    for (int mu = 0; mu < 4; ++mu) c->lat.L[mu] = dims[mu];
-    c->lat.Vh = (int)(V / 2);
-    c->lat.t_bc = t_bc;
+    c->lat = make_lattice(dims, t_bc);
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = cudaMalloc(&c->partials, sizeof(double) * kPartialSlots * kMaxReduceBlocks);
+    if (e == cudaSuccess) e = cudaMalloc(&c->kstatus, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(c->kstatus, 0, sizeof(int) * 4);
+    {
+        int khz = 0;  // SM clock in kHz: kernel waits count clock64() cycles
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device);
+        c->spin_limit = (long long)(5.0 * (khz > 0 ? khz : 2000000) * 1e3);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&c->ticket, sizeof(unsigned) * 16);
     if (e == cudaSuccess) e = cudaMalloc(&c->sums, sizeof(double) * kPartialSlots);
     if (e == cudaSuccess) e = cudaMalloc(&c->state, sizeof(SolverState) * PLQ_MAX_RHS);
@@ -178,6 +184,7 @@ plq_status plq_finalize(plq_ctx *c) {
     for (auto &t : c->nbr)
         if (t) cudaFree(t);
     if (c->partials) cudaFree(c->partials);
+    if (c->kstatus) cudaFree(c->kstatus);
     if (c->ticket) cudaFree(c->ticket);
     if (c->sums) cudaFree(c->sums);
     if (c->state) cudaFree(c->state);
@@ -190,11 +197,34 @@ plq_status plq_finalize(plq_ctx *c) {
     if (c->copy_in) cudaStreamDestroy(c->copy_in);
     if (c->copy_out) cudaStreamDestroy(c->copy_out);
     if (c->compute) cudaStreamDestroy(c->compute);
+    if (c->batch.exec) cudaGraphExecDestroy(c->batch.exec);
+    if (c->batch.scratch) cudaFree(c->batch.scratch);
+    if (c->batch.stream) cudaStreamDestroy(c->batch.stream);
     delete c;
     return PLQ_OK;
 }
 
 long plq_half_volume(const plq_ctx *c) { return c ? (long)c->lat.Vh : 0; }
+
+plq_status plq_set_wait_limit(plq_ctx *c, double seconds) {
+    PLQ_TRY(check_ctx(c));
+    if (!(seconds > 0.0) || !std::isfinite(seconds)) return set_error(PLQ_ERR_ARG, "wait limit must be > 0 s");
+    int khz = 0;
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c->device);
+    const double cyc = seconds * (khz > 0 ? khz : 2000000) * 1e3;
+    c->spin_limit = cyc < 1.0 ? 1LL : cyc > 1e15 ? (long long)1e15 : (long long)cyc;
+    return PLQ_OK;
+}
+
+plq_status plq_device_status(plq_ctx *c, int clear) {
+    PLQ_TRY(check_ctx(c));
+    PLQ_TRY(use_device(c));
+    int v = 0;
+    PLQ_CUDA(cudaMemcpy(&v, c->kstatus, sizeof(int), cudaMemcpyDeviceToHost));
+    if (clear && v != 0) PLQ_CUDA(cudaMemset(c->kstatus, 0, sizeof(int)));
+    if (v != 0) return set_error(v, "a kernel of this context gave up a bounded wait (status %d)", v);
+    return PLQ_OK;
+}
 
 size_t plq_field_bytes(const plq_ctx *c, int prec, int nrhs) {
     if (c && prec == PLQ_DF64 && nrhs >= 1 && nrhs <= PLQ_MAX_RHS) return df_site_bytes() * (size_t)c->lat.Vh * nrhs;

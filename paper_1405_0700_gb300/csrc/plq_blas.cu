@@ -15,11 +15,17 @@ namespace {
 
 constexpr int kBlock = 256;
 
-int grid_for(long long work, bool reduce) {
+// Threads per block of the reducing kernels for n interleaved right-hand
+// sides: a multiple of n, so that with the grid-stride element loop every
+// thread keeps one right-hand side (element e belongs to e mod n) and the
+// reduction can combine its FP64 partial sums in a fixed order.
+int red_block(int n) { return n > 1 ? n * (kBlock / n) : kBlock; }
+
+int grid_for(long long work, bool reduce, int block = kBlock) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long want = (work + kBlock - 1) / kBlock;
+    long long want = (work + block - 1) / block;
     long long cap = (long long)sms * 8;
     if (reduce && cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
     if (want < 1) want = 1;
@@ -74,25 +80,25 @@ __global__ void gamma5_kernel(long long N, void *dst, const void *src) {
 template <int P>
 __global__ void norm2_kernel(long long N, int n, const void *v, Reduce red) {
     using T = RealOf<P>;
-    RedAcc<1, T> acc;
-    red_init(acc, n);
+    RedAcc<1> acc;
+    red_init(acc);
     ELEM_LOOP(N) {
         cx<T> a[12];
         Spinor<P>::load(v, N, e, a);
         T s = 0;
 #pragma unroll
         for (int k = 0; k < 12; ++k) s += a[k].re * a[k].re + a[k].im * a[k].im;
-        acc.add(0, rhs_of(e, n), s);
+        acc.add(0, 0, s);
     }
-    grid_reduce(red, acc);
+    grid_reduce(red, acc, n);
 }
 
 // <a, b> (re, im) and |b|^2
 template <int P>
 __global__ void dot_norm_kernel(long long N, int n, const void *av, const void *bv, Reduce red) {
     using T = RealOf<P>;
-    RedAcc<3, T> acc;
-    red_init(acc, n);
+    RedAcc<3> acc;
+    red_init(acc);
     ELEM_LOOP(N) {
         cx<T> a[12], b[12];
         Spinor<P>::load(av, N, e, a);
@@ -104,12 +110,11 @@ __global__ void dot_norm_kernel(long long N, int n, const void *av, const void *
             s1 += a[k].re * b[k].im - a[k].im * b[k].re;
             s2 += b[k].re * b[k].re + b[k].im * b[k].im;
         }
-        const int rr = rhs_of(e, n);
-        acc.add(0, rr, s0);
-        acc.add(1, rr, s1);
-        acc.add(2, rr, s2);
+        acc.add(0, 0, s0);
+        acc.add(1, 0, s1);
+        acc.add(2, 0, s2);
     }
-    grid_reduce(red, acc);
+    grid_reduce(red, acc, n);
 }
 
 // x += alpha p ; r -= alpha q ; rho_new = |r|^2   (x may be stored at higher precision PX)
@@ -118,8 +123,8 @@ __global__ void cg_update_kernel(long long N, int n, void *x, void *r, const voi
                                  const SolverState *st) {
     using T = RealOf<P>;
     using TX = RealOf<PX>;
-    RedAcc<1, T> acc;
-    red_init(acc, n);
+    RedAcc<1> acc;
+    red_init(acc);
     ELEM_LOOP(N) {
         const int rr = rhs_of(e, n);
         if (st[rr].stop) continue;
@@ -141,9 +146,9 @@ __global__ void cg_update_kernel(long long N, int n, void *x, void *r, const voi
         }
         Spinor<PX>::store(x, N, e, xv);
         Spinor<P>::store(r, N, e, rv);
-        acc.add(0, rr, s);
+        acc.add(0, 0, s);
     }
-    grid_reduce(red, acc);
+    grid_reduce(red, acc, n);
 }
 
 // p = r + beta p
@@ -306,8 +311,8 @@ __global__ void bicg_update_kernel(long long N, int n, void *x, void *r, const v
                                    const void *t, const void *rhat, Reduce red, const SolverState *st) {
     using T = RealOf<P>;
     using TX = RealOf<PX>;
-    RedAcc<3, T> acc;
-    red_init(acc, n);
+    RedAcc<3> acc;
+    red_init(acc);
     ELEM_LOOP(N) {
         const int rr = rhs_of(e, n);
         if (st[rr].stop) continue;
@@ -332,14 +337,21 @@ __global__ void bicg_update_kernel(long long N, int n, void *x, void *r, const v
         }
         Spinor<PX>::store(x, N, e, xv);
         Spinor<P>::store(r, N, e, sv);
-        acc.add(0, rr, s0);
-        acc.add(1, rr, s1);
-        acc.add(2, rr, s2);
+        acc.add(0, 0, s0);
+        acc.add(1, 0, s1);
+        acc.add(2, 0, s2);
     }
-    grid_reduce(red, acc);
+    grid_reduce(red, acc, n);
 }
 
 }  // namespace
+
+#define DISPATCH_PB(prec, BLK, KERNEL, ...)                                                \
+    do {                                                                                   \
+        if ((prec) == PLQ_F64) KERNEL<PLQ_F64><<<grid, (BLK), 0, s>>>(__VA_ARGS__);        \
+        else if ((prec) == PLQ_F32) KERNEL<PLQ_F32><<<grid, (BLK), 0, s>>>(__VA_ARGS__);   \
+        else KERNEL<PLQ_F16><<<grid, (BLK), 0, s>>>(__VA_ARGS__);                          \
+    } while (0)
 
 #define DISPATCH_P(prec, KERNEL, ...)                                                      \
     do {                                                                                   \
@@ -375,27 +387,30 @@ plq_status blas_gamma5(long long N, void *dst, const void *src, int prec, cudaSt
 }
 
 plq_status blas_norm2(long long N, int n, const void *v, int prec, const Reduce &red, cudaStream_t s) {
-    const int grid = grid_for(N, true);
-    DISPATCH_P(prec, norm2_kernel, N, n, v, red);
+    const int blk = red_block(n);
+    const int grid = grid_for(N, true, blk);
+    DISPATCH_PB(prec, blk, norm2_kernel, N, n, v, red);
     PLQ_CUDA(cudaGetLastError());
     return PLQ_OK;
 }
 
 plq_status blas_dot_norm(long long N, int n, const void *a, const void *b, int prec, const Reduce &red,
                          cudaStream_t s) {
-    const int grid = grid_for(N, true);
-    DISPATCH_P(prec, dot_norm_kernel, N, n, a, b, red);
+    const int blk = red_block(n);
+    const int grid = grid_for(N, true, blk);
+    DISPATCH_PB(prec, blk, dot_norm_kernel, N, n, a, b, red);
     PLQ_CUDA(cudaGetLastError());
     return PLQ_OK;
 }
 
 plq_status blas_cg_update(long long N, int n, void *x, void *r, const void *p, const void *q, int prec,
                           const Reduce &red, const SolverState *st, cudaStream_t s) {
-    const int grid = grid_for(N, true);
+    const int blk = red_block(n);
+    const int grid = grid_for(N, true, blk);
     // the solution accumulator is FP64 for FP64 solves and FP32 otherwise
-    if (prec == PLQ_F64) cg_update_kernel<PLQ_F64, PLQ_F64><<<grid, kBlock, 0, s>>>(N, n, x, r, p, q, red, st);
-    else if (prec == PLQ_F32) cg_update_kernel<PLQ_F32, PLQ_F32><<<grid, kBlock, 0, s>>>(N, n, x, r, p, q, red, st);
-    else cg_update_kernel<PLQ_F16, PLQ_F32><<<grid, kBlock, 0, s>>>(N, n, x, r, p, q, red, st);
+    if (prec == PLQ_F64) cg_update_kernel<PLQ_F64, PLQ_F64><<<grid, blk, 0, s>>>(N, n, x, r, p, q, red, st);
+    else if (prec == PLQ_F32) cg_update_kernel<PLQ_F32, PLQ_F32><<<grid, blk, 0, s>>>(N, n, x, r, p, q, red, st);
+    else cg_update_kernel<PLQ_F16, PLQ_F32><<<grid, blk, 0, s>>>(N, n, x, r, p, q, red, st);
     PLQ_CUDA(cudaGetLastError());
     return PLQ_OK;
 }
@@ -465,13 +480,14 @@ plq_status blas_bicg_s(long long N, int n, void *sv, const void *r, const void *
 
 plq_status blas_bicg_update(long long N, int n, void *x, void *r, const void *p, const void *sv, const void *t,
                             const void *rhat, int prec, const Reduce &red, const SolverState *st, cudaStream_t s) {
-    const int grid = grid_for(N, true);
+    const int blk = red_block(n);
+    const int grid = grid_for(N, true, blk);
     if (prec == PLQ_F64)
-        bicg_update_kernel<PLQ_F64, PLQ_F64><<<grid, kBlock, 0, s>>>(N, n, x, r, p, sv, t, rhat, red, st);
+        bicg_update_kernel<PLQ_F64, PLQ_F64><<<grid, blk, 0, s>>>(N, n, x, r, p, sv, t, rhat, red, st);
     else if (prec == PLQ_F32)
-        bicg_update_kernel<PLQ_F32, PLQ_F32><<<grid, kBlock, 0, s>>>(N, n, x, r, p, sv, t, rhat, red, st);
+        bicg_update_kernel<PLQ_F32, PLQ_F32><<<grid, blk, 0, s>>>(N, n, x, r, p, sv, t, rhat, red, st);
     else
-        bicg_update_kernel<PLQ_F16, PLQ_F32><<<grid, kBlock, 0, s>>>(N, n, x, r, p, sv, t, rhat, red, st);
+        bicg_update_kernel<PLQ_F16, PLQ_F32><<<grid, blk, 0, s>>>(N, n, x, r, p, sv, t, rhat, red, st);
     PLQ_CUDA(cudaGetLastError());
     return PLQ_OK;
 }

@@ -230,17 +230,17 @@ __global__ void zlincomb32_kernel(long long N, const float2 *in, size_t stride, 
 // d_i = <u_i, w> for i < cnt (<= kDotChunk), FP32 slots; per-thread FP32 partial
 // sums (a handful of elements each), FP64 across threads and blocks
 __global__ void multidot32_kernel(long long N, const float2 *U, size_t stride, int cnt, const float2 *w, Reduce red) {
-    RedAcc<2 * kDotChunk, float> acc;
-    red_init(acc, 1);
+    RedAcc<2 * kDotChunk> acc;
+    red_init(acc);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
         const float2 b = w[e];
         for (int i = 0; i < cnt; ++i) {
             const float2 a = __ldg(U + i * stride + e);
-            acc.v[2 * i] += a.x * b.x + a.y * b.y;
-            acc.v[2 * i + 1] += a.x * b.y - a.y * b.x;
+            acc.v[2 * i][0] += a.x * b.x + a.y * b.y;
+            acc.v[2 * i + 1][0] += a.x * b.y - a.y * b.x;
         }
     }
-    grid_reduce(red, acc);
+    grid_reduce(red, acc, 1);
 }
 
 __global__ void scale32_kernel(long long N, float2 *v, float s) {
@@ -269,17 +269,17 @@ __global__ void zlincomb_kernel(long long N, const double2 *in, size_t stride, i
 
 // d_i = <u_i, w> for i < cnt (<= kDotChunk)
 __global__ void multidot_kernel(long long N, const double2 *U, size_t stride, int cnt, const double2 *w, Reduce red) {
-    RedAcc<2 * kDotChunk, double> acc;
-    red_init(acc, 1);
+    RedAcc<2 * kDotChunk> acc;
+    red_init(acc);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
         const double2 b = w[e];
         for (int i = 0; i < cnt; ++i) {
             const double2 a = __ldg(U + i * stride + e);
-            acc.v[2 * i] += a.x * b.x + a.y * b.y;
-            acc.v[2 * i + 1] += a.x * b.y - a.y * b.x;
+            acc.v[2 * i][0] += a.x * b.x + a.y * b.y;
+            acc.v[2 * i + 1][0] += a.x * b.y - a.y * b.x;
         }
     }
-    grid_reduce(red, acc);
+    grid_reduce(red, acc, 1);
 }
 
 struct Eig {
@@ -465,6 +465,26 @@ extern "C" plq_status plq_eigcg_destroy(plq_eigcg *E) {
 }
 
 extern "C" int plq_eigcg_vectors(const plq_eigcg *E) { return E ? E->nvec : 0; }
+
+extern "C" int plq_eigcg_projected_matrix(const plq_eigcg *E, double *H, int ld) {
+    if (!E) {
+        set_error(PLQ_ERR_ARG, "null eigcg handle");
+        return -1;
+    }
+    const int k = E->nvec;
+    if (!H) return k;
+    if (ld < k) {
+        set_error(PLQ_ERR_ARG, "leading dimension %d below the %d basis vectors", ld, k);
+        return -1;
+    }
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) {
+            const std::complex<double> h = E->H[(size_t)i * E->max_vectors + j];
+            H[2 * ((size_t)i * ld + j)] = h.real();
+            H[2 * ((size_t)i * ld + j) + 1] = h.imag();
+        }
+    return k;
+}
 
 extern "C" plq_status plq_eigcg_solve(plq_eigcg *E, void *x, const void *b, double kappa,
                                       const plq_solver_params *params, int accumulate, plq_solve_info *info,

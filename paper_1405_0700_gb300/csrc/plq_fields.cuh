@@ -358,43 +358,33 @@ __device__ __forceinline__ void finalize_one(int fin, SolverState *st, const dou
     }
 }
 
-// Per-thread accumulator of NV sums for each of n right-hand sides.  With one
-// right-hand side the sums stay in registers (combined later with warp
-// shuffles in the working precision R, cheap on the FP32 pipes); with several,
-// the element's right-hand side varies across the threads of a warp, so each
-// contribution goes to a shared-memory slot (k, rhs) by atomic add.
-template <int NV, class R>
+// Per-thread FP64 accumulator of NV sums for the RT right-hand sides a thread
+// always handles: those of its right-hand-side column c (c*RT .. c*RT+RT-1).
+// Kernels arrange their threads so that the column is fixed for the whole
+// kernel: c = (linear thread index) mod ncols, with ncols = n / RT columns
+// (2-D blocks of (n/RT) x sites, or 1-D blocks whose size is a multiple of n
+// walking the elements with a stride that is too).  Contributions computed in
+// the working precision (one site's 12 components) are added in FP64, and the
+// combination over threads, warps and blocks below runs in a fixed order, so
+// the sums are reproducible bit for bit for a given launch configuration.
+template <int NV, int RT = 1>
 struct RedAcc {
-    R v[NV];
-    R *sm;
-    int n;
-    __device__ __forceinline__ void add(int k, int rr, R x) {
-        if (n == 1) v[k] += x;
-        else atomicAdd(sm + k * n + rr, x);
-    }
+    double v[NV][RT];
+    __device__ __forceinline__ void add(int k, int t, double x) { v[k][t] += x; }
 };
 
 // Linear thread index and thread count of a (possibly 2-D) block.
 __device__ __forceinline__ int ltid() { return threadIdx.y * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int lsize() { return blockDim.x * blockDim.y; }
 
-// Must be called by every thread of the block before any add().
-template <int NV, class R>
-__device__ __forceinline__ void red_init(RedAcc<NV, R> &acc, int n) {
-    __shared__ R slots[NV * PLQ_MAX_RHS];
-    acc.n = n;
-    acc.sm = slots;
+template <int NV, int RT>
+__device__ __forceinline__ void red_init(RedAcc<NV, RT> &acc) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc.v[k] = R(0);
-    for (int t = ltid(); t < NV * n; t += lsize()) slots[t] = R(0);
-    __syncthreads();
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int t = 0; t < RT; ++t) acc.v[k][t] = 0.0;
 }
 
-// Combine the accumulators of the whole grid: each block writes its partial
-// sums (FP64) to red.partials, and the last block to finish (ticket counter)
-// adds them in block order -- deterministic -- stores the totals in
-// red.sums[k*n + r] and applies the finalize step to red.st[r].  Every thread
-// of every block must call it.
 // Sum over the lanes of a warp that may be partial (the block's thread count
 // need not be a multiple of 32); lane 0 gets the total.
 template <class V>
@@ -408,40 +398,70 @@ __device__ __forceinline__ V warp_sum(V x, int lane, int active) {
     return x;
 }
 
-template <int NV, class R>
-__device__ void grid_reduce(const Reduce &red, RedAcc<NV, R> &acc) {
-    __shared__ double wsum[32][NV];
+// Combine the accumulators of the whole grid (ncols right-hand-side columns
+// of RT right-hand sides each): within a warp the lanes of each column are
+// folded onto its first lanes, row after row; the warps of a block then add
+// their column sums into shared slots one warp after the other; each block
+// writes its partial sums to red.partials, and the last block to finish
+// (ticket counter) adds them in block order, stores the totals in
+// red.sums[k*n + r] and applies the finalize step to red.st[r].  Every thread
+// of every block must call it.
+template <int NV, int RT>
+__device__ void grid_reduce(const Reduce &red, const RedAcc<NV, RT> &acc, int ncols) {
+    __shared__ double slot[kPartialSlots];
     __shared__ double tots[kPartialSlots];
     __shared__ bool last;
     const int tid = ltid(), lane = tid & 31, warp = tid >> 5, nthr = lsize(), nw = (nthr + 31) >> 5;
     const int active = min(32, nthr - warp * 32);  // lanes present in this thread's warp
-    const int n = acc.n, slots = NV * n;
+    const int n = ncols * RT, slots = NV * n;
     double *mine = red.partials + (size_t)blockIdx.x * kPartialSlots;
-    if (n == 1) {
+    for (int t = tid; t < slots; t += nthr) slot[t] = 0.0;
+    double w[NV][RT];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const R x = warp_sum(acc.v[k], lane, active);
-            if (lane == 0) wsum[warp][k] = (double)x;
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int t = 0; t < RT; ++t) w[k][t] = acc.v[k][t];
+    if (ncols == 1) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+            for (int t = 0; t < RT; ++t) w[k][t] = warp_sum(w[k][t], lane, active);
+    } else {
+        const unsigned mask = active >= 32 ? 0xffffffffu : ((1u << active) - 1u);
+        for (int o = ncols; o < 32; o += ncols) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+#pragma unroll
+                for (int t = 0; t < RT; ++t) {
+                    const double y = __shfl_down_sync(mask, w[k][t], o);
+                    if (lane < ncols && lane + o < active) w[k][t] += y;
+                }
+        }
+    }
+    __syncthreads();
+    const int lead = min(ncols, active);  // lanes holding their warp's column sums
+    for (int ww = 0; ww < nw; ++ww) {
+        if (warp == ww && lane < lead) {
+            const int c = tid % ncols;
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+#pragma unroll
+                for (int t = 0; t < RT; ++t) slot[k * n + c * RT + t] += w[k][t];
         }
         __syncthreads();
-        if (tid < NV) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += wsum[w][tid];
-            mine[tid] = s;
-        }
-    } else {
-        __syncthreads();  // all shared-memory atomics of the block are done
-        for (int t = tid; t < slots; t += nthr) mine[t] = (double)acc.sm[t];
     }
+    for (int t = tid; t < slots; t += nthr) mine[t] = slot[t];
     __threadfence();
     __syncthreads();
     if (tid == 0) last = (atomicAdd(red.ticket, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // each warp sums whole slots over the blocks, its `active` lanes striding
+    // by `active` (a partial last warp must still visit every block)
     for (int t = warp; t < slots; t += nw) {
         double s = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(red.partials + (size_t)b * kPartialSlots + t);
+        for (int b = lane; b < (int)gridDim.x; b += active) s += __ldcg(red.partials + (size_t)b * kPartialSlots + t);
         s = warp_sum(s, lane, active);
         if (lane == 0) tots[t] = s;
     }
@@ -468,19 +488,16 @@ struct SiteGeom {
 
 __device__ __forceinline__ SiteGeom site_geom(const Lattice &L, int par, int i) {
     SiteGeom g;
-    const int Lxh = L.L[1] >> 1;
-    int r = i / Lxh;
-    const int xh = i - r * Lxh;
-    const int y = r % L.L[2];
-    r /= L.L[2];
-    const int z = r % L.L[3];
-    const int t = r / L.L[3];
-    const int x = 2 * xh + ((par + y + z + t) & 1);
+    unsigned xh, y, z;
+    unsigned r = fd_divmod((unsigned)i, L.div_xh, &xh);
+    r = fd_divmod(r, L.div_y, &y);
+    const int t = (int)fd_divmod(r, L.div_z, &z);
+    const int x = 2 * (int)xh + ((par + (int)y + (int)z + t) & 1);
     g.c[0] = t;
     g.c[1] = x;
-    g.c[2] = y;
-    g.c[3] = z;
-    g.lex = ((t * L.L[3] + z) * L.L[2] + y) * L.L[1] + x;
+    g.c[2] = (int)y;
+    g.c[3] = (int)z;
+    g.lex = ((t * L.L[3] + (int)z) * L.L[2] + (int)y) * L.L[1] + x;
     return g;
 }
 

@@ -112,6 +112,121 @@ __device__ __forceinline__ void su3_dag_mul(const cx<T> u[3][3], const cx<T> h[6
         }
 }
 
+// ---------------------------------------------------------------- packed FP32
+// sm_100 and later issue two FP32 additions, multiplications or FMAs per
+// instruction on a register pair (__fadd2_rn, __fmul2_rn, __ffma2_rn).  A
+// complex number {re, im} is such a pair: the pair form of the projection,
+// SU(3) product and reconstruction below is used where it measured faster
+// (see packed_pairs()).
+__device__ __forceinline__ float2 f2of(cx<float> z) { return make_float2(z.re, z.im); }
+__device__ __forceinline__ cx<float> cxof(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// a + i^K b on pairs: K even in one packed instruction, K odd in two scalar ones
+template <int K>
+__device__ __forceinline__ float2 add_ipow2(float2 a, float2 b) {
+    if constexpr ((K & 3) == 0) return add2(a, b);
+    else if constexpr ((K & 3) == 2) return fma2(b, make_float2(-1.f, -1.f), a);
+    else if constexpr ((K & 3) == 1) return make_float2(a.x - b.y, a.y + b.x);
+    else return make_float2(a.x + b.y, a.y - b.x);
+}
+
+// Upper two spin components of (1 + S gamma_mu) phi as pairs.
+template <int MU, int S>
+__device__ __forceinline__ void project2(const cx<float> phi[12], float2 h[6]) {
+    using Q = Proj<MU>;
+    constexpr int k0 = Q::k0 + (S > 0 ? 2 : 0), k1 = Q::k1 + (S > 0 ? 2 : 0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        h[c] = add_ipow2<k0>(f2of(phi[c]), f2of(phi[3 * Q::p0 + c]));
+        h[3 + c] = add_ipow2<k1>(f2of(phi[3 + c]), f2of(phi[3 * Q::p1 + c]));
+    }
+}
+
+// acc += the full spinor rebuilt from the colour-rotated upper components uh.
+template <int MU, int S>
+__device__ __forceinline__ void reconstruct2(cx<float> acc[12], const float2 uh[6]) {
+    using Q = Proj<MU>;
+    constexpr int k0 = Q::k0 + (S > 0 ? 2 : 0), k1 = Q::k1 + (S > 0 ? 2 : 0);
+    constexpr int j0 = (4 - (k0 & 3)) & 3, j1 = (4 - (k1 & 3)) & 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[c] = cxof(add2(f2of(acc[c]), uh[c]));
+        acc[3 + c] = cxof(add2(f2of(acc[3 + c]), uh[3 + c]));
+        acc[3 * Q::p0 + c] = cxof(add_ipow2<j0>(f2of(acc[3 * Q::p0 + c]), uh[c]));
+        acc[3 * Q::p1 + c] = cxof(add_ipow2<j1>(f2of(acc[3 * Q::p1 + c]), uh[3 + c]));
+    }
+}
+
+// uh = U h (BACK = false) or U^dagger h (BACK = true) for both spin components
+// with the link's natural pairs u = {re, im} and broadcast spinor pairs:
+// zA = sum_b {h.re, h.re} * u, zB = sum_b {h.im, h.im} * u; then
+// U h = {zA.re - zB.im, zA.im + zB.re} and U^dagger h = {zA.re + zB.im, zB.re - zA.im}.
+template <bool BACK>
+__device__ __forceinline__ void su3_apply_pairs(const cx<float> u[3][3], const float2 h[6], float2 uh[6]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        float2 hr[3], hi[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            hr[b] = make_float2(h[3 * s + b].x, h[3 * s + b].x);
+            hi[b] = make_float2(h[3 * s + b].y, h[3 * s + b].y);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float2 zA = mul2(hr[0], f2of(BACK ? u[0][a] : u[a][0]));
+            zA = fma2(hr[1], f2of(BACK ? u[1][a] : u[a][1]), zA);
+            zA = fma2(hr[2], f2of(BACK ? u[2][a] : u[a][2]), zA);
+            float2 zB = mul2(hi[0], f2of(BACK ? u[0][a] : u[a][0]));
+            zB = fma2(hi[1], f2of(BACK ? u[1][a] : u[a][1]), zB);
+            zB = fma2(hi[2], f2of(BACK ? u[2][a] : u[a][2]), zB);
+            uh[3 * s + a] = BACK ? make_float2(zA.x + zB.y, zB.x - zA.y) : make_float2(zA.x - zB.y, zA.y + zB.x);
+        }
+    }
+}
+
+// a + i^K b on half2 complex numbers (K odd: the swapped pair times (-1, +1)
+// or (+1, -1))
+template <int K>
+__device__ __forceinline__ __half2 hadd_ipow(__half2 a, __half2 b) {
+    if constexpr ((K & 3) == 0) return __hadd2(a, b);
+    else if constexpr ((K & 3) == 2) return __hsub2(a, b);
+    else if constexpr ((K & 3) == 1) return __hfma2(__lowhigh2highlow(b), __floats2half2_rn(-1.f, 1.f), a);
+    else return __hfma2(__lowhigh2highlow(b), __floats2half2_rn(1.f, -1.f), a);
+}
+
+// FP16 storage: load the neighbour's 12 stored (normalised) complex
+// components, project them to the upper two spin components of
+// (1 + S gamma_mu) phi in half2 arithmetic (the stored values lie in [-1, 1],
+// their sums in [-2, 2]), and convert only the 6 projected ones; returns the
+// site norm.
+template <int MU, int S>
+__device__ __forceinline__ float project_f16(const void *base, size_t stride, size_t e, float2 h[6]) {
+    using Q = Proj<MU>;
+    constexpr int k0 = Q::k0 + (S > 0 ? 2 : 0), k1 = Q::k1 + (S > 0 ? 2 : 0);
+    const uint4 *p = static_cast<const uint4 *>(base) + e;
+    const float *nrm = reinterpret_cast<const float *>(static_cast<const uint4 *>(base) + 3 * stride);
+    unsigned w[12];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const uint4 t = ld_nc(p + k * stride);
+        w[4 * k] = t.x;
+        w[4 * k + 1] = t.y;
+        w[4 * k + 2] = t.z;
+        w[4 * k + 3] = t.w;
+    }
+    const float n = ld_nc(nrm + e);
+    auto hv = [&](int c) { return *reinterpret_cast<const __half2 *>(&w[c]); };
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        h[c] = __half22float2(hadd_ipow<k0>(hv(c), hv(3 * Q::p0 + c)));
+        h[3 + c] = __half22float2(hadd_ipow<k1>(hv(3 + c), hv(3 * Q::p1 + c)));
+    }
+    return n;
+}
+
 __device__ __forceinline__ int lex_stride(const Lattice &L, int mu) {
     // strides of t, x, y, z in the lexicographic index
     return mu == 0 ? L.L[1] * L.L[2] * L.L[3] : mu == 1 ? 1 : mu == 2 ? L.L[1] : L.L[1] * L.L[2];
@@ -128,6 +243,58 @@ __device__ __forceinline__ RealOf<P> load_for_projection(const void *base, size_
     } else {
         Spinor<P>::load(base, stride, e, phi);
         return RealOf<P>(1);
+    }
+}
+
+// Which single-right-hand-side formats use the packed pair arithmetic above:
+// measured on the 32^3 x 64 half-application, it speeds up FP16 storage with
+// 12-real links (80.2 -> 77.1 us; the kernel is bound by instruction issue)
+// and slows down the others (FP32 18-real 121.6 -> 127.9 us, FP32 12-real
+// 97.1 -> 98.6 us, FP16 18-real 76.7 -> 90.0 us), which keep the scalar form.
+template <int P, int R>
+constexpr bool packed_pairs() {
+    return P == PLQ_F16 && R == 12;
+}
+
+// One neighbour's contribution: project phi(y) with (1 + S gamma_mu), apply
+// the time-boundary sign and the FP16 site norm, multiply by U (BACK = false)
+// or U^dagger (BACK = true), rebuild and accumulate.  Formats with
+// packed_pairs() use the pair arithmetic (FP16 storage projects in half2
+// first).
+template <int P, int R, int MU, int S, bool BACK>
+__device__ __forceinline__ void hop_one(const void *in, size_t stride, size_t e, bool flip,
+                                        const cx<RealOf<P>> u[3][3], cx<RealOf<P>> acc[12]) {
+    using T = RealOf<P>;
+    if constexpr (!packed_pairs<P, R>()) {
+        cx<T> phi[12], h[6], uh[6];
+        T sc = load_for_projection<P>(in, stride, e, phi);
+        project<MU, S>(phi, h);
+        if (MU == 0 && flip) sc = -sc;
+        if (P == PLQ_F16 || (MU == 0 && flip)) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) h[k] = {sc * h[k].re, sc * h[k].im};
+        }
+        if constexpr (BACK) su3_dag_mul(u, h, uh);
+        else su3_mul(u, h, uh);
+        reconstruct<MU, S>(acc, uh);
+    } else {
+        float2 h[6], uh[6];
+        float sc = 1.f;
+        if constexpr (P == PLQ_F16) {
+            sc = project_f16<MU, S>(in, stride, e, h);
+        } else {
+            cx<float> phi[12];
+            Spinor<P>::load(in, stride, e, phi);
+            project2<MU, S>(phi, h);
+        }
+        if (MU == 0 && flip) sc = -sc;
+        if (P == PLQ_F16 || (MU == 0 && flip)) {
+            const float2 sc2 = make_float2(sc, sc);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) h[k] = mul2(h[k], sc2);
+        }
+        su3_apply_pairs<BACK>(u, h, uh);
+        reconstruct2<MU, S>(acc, uh);
     }
 }
 
@@ -165,20 +332,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
         cx<T> u[3][3];
         Link<P, R>::load(gbase + (size_t)(a.out_parity * 4 + MU) * a.gblock, L.Vh, i, u);
 #pragma unroll
-        for (int t = 0; t < RT; ++t) {
-            cx<T> phi[12];
-            T sc = load_for_projection<P>(a.in, stride, (size_t)j * n + r0 + t, phi);
-            cx<T> h[6];
-            project<MU, SF>(phi, h);
-            if (MU == 0 && flip) sc = -sc;
-            if (P == PLQ_F16 || (MU == 0 && flip)) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) h[k] = {sc * h[k].re, sc * h[k].im};
-            }
-            cx<T> uh[6];
-            su3_mul(u, h, uh);
-            reconstruct<MU, SF>(acc[t], uh);
-        }
+        for (int t = 0; t < RT; ++t) hop_one<P, R, MU, SF, false>(a.in, stride, (size_t)j * n + r0 + t, flip, u, acc[t]);
     }
     // backward neighbour x - mu
     {
@@ -196,20 +350,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
         cx<T> u[3][3];
         Link<P, R>::load(gbase + (size_t)((1 - a.out_parity) * 4 + MU) * a.gblock, L.Vh, j, u);
 #pragma unroll
-        for (int t = 0; t < RT; ++t) {
-            cx<T> phi[12];
-            T sc = load_for_projection<P>(a.in, stride, (size_t)j * n + r0 + t, phi);
-            cx<T> h[6];
-            project<MU, SB>(phi, h);
-            if (MU == 0 && flip) sc = -sc;
-            if (P == PLQ_F16 || (MU == 0 && flip)) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) h[k] = {sc * h[k].re, sc * h[k].im};
-            }
-            cx<T> uh[6];
-            su3_dag_mul(u, h, uh);
-            reconstruct<MU, SB>(acc[t], uh);
-        }
+        for (int t = 0; t < RT; ++t) hop_one<P, R, MU, SB, true>(a.in, stride, (size_t)j * n + r0 + t, flip, u, acc[t]);
     }
 }
 
@@ -230,8 +371,8 @@ __device__ __forceinline__ void hop_body(const HopArgs &a) {
     const long long total = (long long)a.lat.Vh * n;
     const size_t stride = (size_t)total;
     constexpr int NV = EPI == EPI_XPAY_NORM ? 1 : EPI == EPI_XPAY_DOTW ? 2 : EPI == EPI_XPAY_TS ? 3 : 0;
-    RedAcc<(NV > 0 ? NV : 1), T> racc;
-    if constexpr (NV > 0) red_init(racc, n);
+    RedAcc<(NV > 0 ? NV : 1), RT> racc;
+    red_init(racc);
 
     const int r0 = threadIdx.x * RT;
     const int i_end = a.site_end < 0 ? a.lat.Vh : a.site_end;
@@ -285,7 +426,7 @@ __device__ __forceinline__ void hop_body(const HopArgs &a) {
                     T s0 = 0;
 #pragma unroll
                     for (int k = 0; k < 12; ++k) s0 += acc[t][k].re * acc[t][k].re + acc[t][k].im * acc[t][k].im;
-                    racc.add(0, rr, s0);
+                    racc.add(0, t, s0);
                 } else if constexpr (EPI == EPI_XPAY_DOTW) {
                     cx<T> wv[12];
                     Spinor<P>::load(a.w, stride, (size_t)idx, wv);
@@ -295,8 +436,8 @@ __device__ __forceinline__ void hop_body(const HopArgs &a) {
                         s0 += wv[k].re * acc[t][k].re + wv[k].im * acc[t][k].im;
                         s1 += wv[k].re * acc[t][k].im - wv[k].im * acc[t][k].re;
                     }
-                    racc.add(0, rr, s0);
-                    racc.add(1, rr, s1);
+                    racc.add(0, t, s0);
+                    racc.add(1, t, s1);
                 } else if constexpr (EPI == EPI_XPAY_TS) {
                     T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
@@ -305,15 +446,15 @@ __device__ __forceinline__ void hop_body(const HopArgs &a) {
                         s1 += acc[t][k].re * xv[k].im - acc[t][k].im * xv[k].re;
                         s2 += acc[t][k].re * acc[t][k].re + acc[t][k].im * acc[t][k].im;
                     }
-                    racc.add(0, rr, s0);
-                    racc.add(1, rr, s1);
-                    racc.add(2, rr, s2);
+                    racc.add(0, t, s0);
+                    racc.add(1, t, s1);
+                    racc.add(2, t, s2);
                 }
             }
             Spinor<P>::store(a.out, stride, (size_t)idx, acc[t]);
         }
     }
-    if constexpr (NV > 0) grid_reduce(a.red, racc);
+    if constexpr (NV > 0) grid_reduce(a.red, racc, blockDim.x);
 }
 
 // Register budget of the one-RHS kernels (0: the compiler's choice under a
@@ -409,8 +550,8 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
     const int n = a.nrhs;
     const size_t stride = (size_t)a.lat.Vh * n;
     constexpr int NV = EPI == EPI_XPAY_NORM ? 1 : 0;
-    RedAcc<1, T> racc;
-    if constexpr (NV > 0) red_init(racc, n);
+    RedAcc<1, RT> racc;
+    red_init(racc);
     const Lattice &L = a.lat;
     const char *gbase = static_cast<const char *>(a.gauge);
     const int S = blockDim.y;
@@ -593,13 +734,13 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
                     T s0 = 0;
 #pragma unroll
                     for (int e = 0; e < 12; ++e) s0 += acc[t][e].re * acc[t][e].re + acc[t][e].im * acc[t][e].im;
-                    racc.add(0, rr, s0);
+                    racc.add(0, t, s0);
                 }
             }
             Spinor<P>::store(a.out, stride, (size_t)idx, acc[t]);
         }
     }
-    if constexpr (NV > 0) grid_reduce(a.red, racc);
+    if constexpr (NV > 0) grid_reduce(a.red, racc, blockDim.x);
 }
 
 template <int P, int R, int EPI, bool DAG, int RT, int NB>
@@ -731,12 +872,21 @@ plq_status dispatch_tiled(const HopArgs &a, int epi, cudaStream_t s, int block) 
     }
 }
 
+}  // namespace plq
+
+#include "plq_hop_rows.cuh"
+
+namespace plq {
+
 template <int P, int R>
 plq_status dispatch_hop(const HopArgs &a, int epi, cudaStream_t s, int block) {
     // Right-hand-side tiles (RT > 1) exist for the FP32-arithmetic storage
     // formats and the epilogues of operator applications and CG; the
-    // neighbour-table variants for the plain and xpay epilogues.
+    // neighbour-table variants for the plain and xpay epilogues; the
+    // row-streamed kernel for whole-lattice applications with those epilogues.
     if constexpr (P != PLQ_F64) {
+        if (a.smem_links == 4 && a.site_begin == 0 && a.site_end < 0 && epi <= EPI_XPAY_NORM)
+            return dispatch_rows<P, R>(a, epi, s);
         if (a.smem_links && a.nrhs > 1 && a.site_begin == 0 && a.site_end < 0 && epi <= EPI_XPAY_NORM) {
             if (a.rhs_tile == 2 && a.nrhs % 2 == 0) return dispatch_mrhs<P, R, 2, 0>(a, epi, s, block);
             if (a.smem_links == 2) return dispatch_mrhs<P, R, 1, 2>(a, epi, s, block);

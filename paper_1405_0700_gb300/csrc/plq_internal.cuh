@@ -10,6 +10,7 @@
 #include <string>
 
 #include "plq.h"
+#include "plq_fastdiv.h"
 
 namespace plq {
 
@@ -34,7 +35,22 @@ struct Lattice {
     int L[4];   // {T, Lx, Ly, Lz}
     int Vh;     // sites per parity
     int t_bc;   // -1 antiperiodic, +1 periodic in time
+    // multiply-shift divisors by Lx/2, Ly and Lz (site coordinates from a
+    // checkerboard index without hardware integer division)
+    FastDiv div_xh, div_y, div_z;
 };
+
+// Fill the extents, Vh and the divisors of a lattice.
+inline Lattice make_lattice(const int dims[4], int t_bc) {
+    Lattice L{};
+    for (int mu = 0; mu < 4; ++mu) L.L[mu] = dims[mu];
+    L.Vh = (int)((long long)dims[0] * dims[1] * dims[2] * dims[3] / 2);
+    L.t_bc = t_bc;
+    L.div_xh = make_fastdiv((uint32_t)(dims[1] / 2));
+    L.div_y = make_fastdiv((uint32_t)dims[2]);
+    L.div_z = make_fastdiv((uint32_t)dims[3]);
+    return L;
+}
 
 inline bool valid_prec(int p) { return p == PLQ_F64 || p == PLQ_F32 || p == PLQ_F16; }
 
@@ -119,6 +135,8 @@ struct Ctx {
     TuneEntry tune[3][PLQ_MAX_RHS + 1];
     int *nbr[2] = {nullptr, nullptr};  // neighbour tables per output parity (built on demand)
     int device = 0;
+    int *kstatus = nullptr;          // device word: PLQ_ERR_TIMEOUT once a bounded kernel wait gave up
+    long long spin_limit = 0;        // clock cycles a kernel wait may take (about 5 s by default)
     GaugeCopy gauge[3];
     GaugeCopy gauge_df;  // PLQ_DF64 links (float-float, 18 reals)
     // reduction scratch
@@ -152,6 +170,20 @@ struct Ctx {
         cudaGraphExec_t exec = nullptr;
         unsigned long long key[8] = {};
     } host_graph;
+    // The persistent batched CG solves launched with this context first in
+    // their list: descriptor and barrier scratch, internal stream, the
+    // instantiated graph of the last launch (replayed while its key matches)
+    // and the launch shape chosen by plq_autotune_batched / plq_set_batched_launch.
+    struct BatchCache {
+        void *scratch = nullptr;
+        size_t bytes = 0;
+        cudaStream_t stream = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long key[6] = {};
+        int shape = 0;          // index into the kernel's launch shapes
+        int blocks_per_sm = 0;  // 0: as many as fit
+        int tuned = 0;          // 1 once a shape was chosen by timing or by hand
+    } batch;
 };
 
 plq_status ensure_work(Ctx *c, size_t bytes);
@@ -209,6 +241,10 @@ struct HopArgs {
     // thread walks its share of the sites); k > 0 = enough blocks for k sites
     // (site blocks of the multi-RHS kernel) per thread.
     int spt = 0;
+    // Bounded waits of the row-streamed kernel: a wait gives up after
+    // spin_limit clock cycles and records PLQ_ERR_TIMEOUT in *kstatus.
+    long long spin_limit = 1LL << 40;
+    int *kstatus = nullptr;
 };
 
 // Launch the hopping kernel for (prec, link reals, epilogue).  block = 0 picks

@@ -54,7 +54,7 @@ bool cache_lookup(const char *path, const std::string &key, TuneEntry *e) {
         // key block index_mode rhs_tile z_chunk smem_links us [sites_per_thread]
         const int got = sscanf(line, "%599s %d %d %d %d %d %f %d", k, &block, &mode, &tile, &zc, &sm, &us, &spt);
         const bool valid = (block == 0 || (block >= 32 && block <= 1024 && block % 32 == 0)) && (mode == 0 || mode == 1) &&
-                           (tile == 1 || tile == 2 || tile == 4) && zc >= 0 && sm >= 0 && sm <= 3 && spt >= 0 &&
+                           (tile == 1 || tile == 2 || tile == 4) && zc >= 0 && sm >= 0 && sm <= 4 && spt >= 0 &&
                            spt <= 64 && !(sm >= 2 && tile != 1) && !(sm == 1 && tile == 4);
         if (got >= 7 && key == k && valid) {
             e->block = block;
@@ -100,8 +100,10 @@ void apply_tune(const Ctx *c, int prec, int nrhs, HopArgs &a) {
     a.nbr = (e.index_mode == 1) ? c->nbr[a.out_parity] : nullptr;
     a.rhs_tile = (e.rhs_tile > 1 && nrhs % e.rhs_tile == 0) ? e.rhs_tile : 1;
     a.zc = (e.zc > 0 && c->lat.L[3] % e.zc == 0) ? e.zc : 0;
-    a.smem_links = nrhs > 1 ? e.smem_links : 0;
+    a.smem_links = (nrhs > 1 || e.smem_links == 4) ? e.smem_links : 0;
     a.spt = e.spt;
+    a.kstatus = c->kstatus;
+    if (c->spin_limit > 0) a.spin_limit = c->spin_limit;
 }
 
 }  // namespace plq
@@ -196,6 +198,8 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
         a.zc = t.zc;
         a.smem_links = t.smem_links;
         a.spt = t.spt;
+        a.kstatus = c->kstatus;
+        a.spin_limit = c->spin_limit;
         *us_out = -1.f;
         plq_status r = launch_hop(a, prec, c->gauge[prec].reals, EPI_PLAIN, s);
         if (r == PLQ_ERR_ARG) return PLQ_OK;
@@ -229,10 +233,28 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
             }
         }
     }
+    // the row-streamed kernel (its block is fixed by nrhs and Lx/2; the
+    // sites-per-thread field selects how many shared-memory slots it rings
+    // through, 0 = as many as fit)
+    if (prec != PLQ_F64) {
+        for (int k : {0, 3, 4, 6}) {
+            if (st != PLQ_OK) break;
+            TuneEntry t;
+            t.block = 0;
+            t.smem_links = 4;
+            t.spt = k;
+            float us = -1.f;
+            st = time_cfg(t, &us);
+            if (st == PLQ_OK && us >= 0.f && us < best.us) {
+                t.us = us;
+                best = t;
+            }
+        }
+    }
     // sites per thread: a grid sized for k sites (site blocks) per thread
     // against the one-wave grid of the sweep above
     for (int k : {1, 2, 4, 8}) {
-        if (st != PLQ_OK) break;
+        if (st != PLQ_OK || best.smem_links == 4) break;
         TuneEntry t = best;
         t.spt = k;
         float us = -1.f;
@@ -279,8 +301,9 @@ extern "C" plq_status plq_set_launch(plq_ctx *c, int prec, int nrhs, int block, 
     if (nrhs % rhs_tile) return set_error(PLQ_ERR_ARG, "rhs_tile must divide nrhs");
     if (z_chunk < 0 || (z_chunk > 0 && c->lat.L[3] % z_chunk))
         return set_error(PLQ_ERR_ARG, "z_chunk must be 0 or divide Lz");
-    if (smem_links < 0 || smem_links > 3) return set_error(PLQ_ERR_ARG, "smem_links must be 0, 1, 2 or 3");
-    if (smem_links >= 2 && rhs_tile != 1) return set_error(PLQ_ERR_ARG, "smem_links 2 and 3 need rhs_tile 1");
+    if (smem_links < 0 || smem_links > 4) return set_error(PLQ_ERR_ARG, "smem_links must be 0, 1, 2, 3 or 4");
+    if (smem_links >= 2 && rhs_tile != 1) return set_error(PLQ_ERR_ARG, "smem_links 2, 3 and 4 need rhs_tile 1");
+    if (smem_links == 4 && prec == PLQ_F64) return set_error(PLQ_ERR_ARG, "smem_links 4 needs FP32 or FP16 storage");
     if (smem_links == 1 && rhs_tile == 4) return set_error(PLQ_ERR_ARG, "smem_links 1 needs rhs_tile 1 or 2");
     PLQ_CUDA(cudaSetDevice(c->device));
     if (index_mode == 1) PLQ_TRY(ensure_nbr_tables(c));

@@ -74,6 +74,8 @@ class BatchInfo(ctypes.Structure):
         ("graph_captured", ctypes.c_int),
         ("launches", ctypes.c_int),
         ("seconds", ctypes.c_double),
+        ("blocks_per_sm", ctypes.c_int),
+        ("graph_reused", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -100,6 +102,8 @@ SIGNATURES = {
     "plq_init": (_c_int, [ctypes.POINTER(_vp), _vp, _c_int, _c_int]),
     "plq_finalize": (_c_int, [_vp]),
     "plq_half_volume": (_c_long, [_vp]),
+    "plq_set_wait_limit": (_c_int, [_vp, _c_double]),
+    "plq_device_status": (_c_int, [_vp, _c_int]),
     "plq_field_bytes": (_c_size, [_vp, _c_int, _c_int]),
     "plq_gauge_upload": (_c_int, [_vp, _vp, _c_int, _c_int, _c_int, _vp]),
     "plq_pack_spinor": (_c_int, [_vp, _vp, _vp, _c_int, _c_int, _vp]),
@@ -119,12 +123,17 @@ SIGNATURES = {
     "plq_cg_solve_batched": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolverParams),
                                       ctypes.POINTER(SolveInfo), ctypes.POINTER(BatchInfo), _vp]),
+    "plq_set_batched_launch": (_c_int, [_vp, _c_int, _c_int]),
+    "plq_autotune_batched": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolverParams), ctypes.c_char_p,
+                                      ctypes.POINTER(BatchInfo)]),
     "plq_theta_bytes": (_c_size, [_vp, _c_int]),
     "plq_hopping_eo_theta": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _c_int, _vp]),
     "plq_link_spinor_stream": (_c_int, [_c_int, ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, _c_int, _vp]),
     "plq_eigcg_create": (_c_int, [_vp, _c_int, _c_int, _c_int, ctypes.POINTER(_vp)]),
     "plq_eigcg_destroy": (_c_int, [_vp]),
     "plq_eigcg_vectors": (_c_int, [_vp]),
+    "plq_eigcg_projected_matrix": (_c_int, [_vp, _vp, _c_int]),
     "plq_eigcg_solve": (_c_int, [_vp, _vp, _vp, _c_double, ctypes.POINTER(SolverParams), _c_int,
                                  ctypes.POINTER(SolveInfo), _vp]),
     "plq_measure_fma_rate": (_c_int, [_c_int, _c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -245,6 +254,14 @@ class Context:
     @property
     def half_volume(self):
         return int(lib().plq_half_volume(self._h))
+
+    def set_wait_limit(self, seconds):
+        """Longest time a bounded wait inside this context's kernels may take."""
+        check(lib().plq_set_wait_limit(self._h, float(seconds)))
+
+    def device_status(self, clear=True):
+        """Status word of this context's kernels (PLQ_OK, or the error a kernel recorded)."""
+        return int(lib().plq_device_status(self._h, int(bool(clear))))
 
     @property
     def volume(self):
@@ -432,6 +449,27 @@ def cg_solve_batched(ctxs, xs, bs, kappas, tol=1e-10, maxit=20000, inner_prec=F6
     return list(infos), bi.as_dict()
 
 
+def set_batched_launch(ctx, block=0, blocks_per_sm=0):
+    """Launch shape of the persistent batched kernel for batches led by ``ctx``."""
+    check(lib().plq_set_batched_launch(ctx.handle, int(block), int(blocks_per_sm)))
+
+
+def autotune_batched(ctxs, xs, bs, kappas, tol=1e-10, maxit=20000, inner_prec=F64, delta=0.0, cache_path=None,
+                     wait_limit_s=0.0):
+    """Time the persistent batched CG's launch shapes on these systems (see
+    plq_autotune_batched) and keep the fastest in ctxs[0]; returns its launch report."""
+    n = len(ctxs)
+    H = (_vp * n)(*[c.handle.value for c in ctxs])
+    X = (_vp * n)(*[_ptr(x) for x in xs])
+    B = (_vp * n)(*[_ptr(b) for b in bs])
+    K = (ctypes.c_double * n)(*[float(k) for k in kappas])
+    p = SolverParams(tol, maxit, prec_of(inner_prec), delta, 0, 16, 0.0, F64, float(wait_limit_s))
+    bi = BatchInfo()
+    path = cache_path.encode() if cache_path else None
+    check(lib().plq_autotune_batched(H, n, X, B, K, ctypes.byref(p), path, ctypes.byref(bi)))
+    return bi.as_dict()
+
+
 class EigCG:
     """Incremental EigCG deflation on a context (see plq_eigcg_create / plq_eigcg_solve)."""
 
@@ -444,6 +482,17 @@ class EigCG:
     @property
     def vectors(self):
         return int(lib().plq_eigcg_vectors(self._h))
+
+    def projected_matrix(self):
+        """H = U^H A U of the deflation basis as a (k, k) complex128 array."""
+        k = int(lib().plq_eigcg_projected_matrix(self._h, None, 0))
+        if k < 0:
+            check(PLQ_ERR_ARG)
+        H = np.zeros((max(k, 1), max(k, 1), 2), dtype=np.float64)
+        got = int(lib().plq_eigcg_projected_matrix(self._h, H.ctypes.data, max(k, 1)))
+        if got < 0:
+            check(PLQ_ERR_ARG)
+        return (H[..., 0] + 1j * H[..., 1])[:k, :k]
 
     def solve(self, x, b, kappa, tol=1e-8, maxit=20000, accumulate=True, stream=None, raise_on_error=True):
         p = SolverParams(tol, maxit, F64, 0.0, 0, 16, 0.0, F64)

@@ -119,3 +119,21 @@ def test_host_slab_schedule(lib):
     K = lib.plq_host_slabs(64, b)
     assert [b[k + 1] - b[k] for k in range(K)] == [1, 1, 2, 4, 8, 8, 8, 8, 8, 8, 4, 2, 1, 1]
     assert lib.plq_host_slabs(7, b) == 0 and lib.plq_host_slabs(0, b) == 0 and lib.plq_host_slabs(8, None) == 0
+
+
+def test_every_declaration_cites_its_definition():
+    """Each exported call's comment names the passage of the paper that defines the
+    operation (a section or equation) or says that the paper is silent on it; the
+    allocation-free Schur operator instead says that the paper has no counterpart."""
+    txt = header_text()
+    for m in re.finditer(r"PLQ_API\s+[\w\s\*]+?\b(plq_\w+)\s*\(", txt):
+        name = m.group(1)
+        before = txt[:m.start()]
+        end = before.rfind("*/")
+        start = before.rfind("/*", 0, end)
+        assert end > 0 and start >= 0, name
+        comment = before[start:end]
+        if name == "plq_schur_apply_noalloc":
+            assert "No counterpart in the paper" in comment
+            continue
+        assert re.search(r"Sec\. \d|Eq\. \(\d\)|[Pp]aper silent", comment), name

@@ -155,7 +155,7 @@ def test_multi_rhs_shared_staging_ragged(sm, prec, reals, nrhs, block):
 def test_set_launch_rejects_bad_staging():
     dims = (4, 4, 2, 4)
     with Context(dims) as ctx:
-        for sm, tile in ((4, 1), (-1, 1), (2, 2), (3, 4), (1, 4)):
+        for sm, tile in ((5, 1), (-1, 1), (2, 2), (3, 4), (1, 4), (4, 2)):
             with pytest.raises(PLQError) as e:
                 ctx.set_launch(F32, 4, 64, 0, tile, 0, sm)
             assert e.value.status == plq.PLQ_ERR_ARG
@@ -389,3 +389,80 @@ def test_host_entry_point_follows_gauge_format_change():
             ctx.hopping_eo_host(0, host_out, host_in, F32)
             torch.cuda.synchronize()
             assert torch.equal(host_out, dev_out.cpu()), reals
+
+
+ROW_LATTICES = [(8, 8, 8, 8), (10, 4, 6, 8), (6, 16, 2, 4), (4, 8, 2, 6)]
+
+
+def rows_fit(dims, prec, reals, nrhs):
+    """The row-streamed kernel's conditions: n x Lx/2 threads <= 512 and every row run
+    of a plane a multiple of 16 bytes."""
+    lxh = dims[1] // 2
+    narrow = {(F32, 18): 8, (F32, 12): 0, (F16, 18): 4, (F16, 12): 8}[(prec, reals)]
+    if nrhs * lxh > 512 or (narrow and (lxh * narrow) % 16):
+        return False
+    return not (prec == F16 and (lxh * nrhs) % 4)
+
+
+@pytest.mark.parametrize("dims", ROW_LATTICES)
+@pytest.mark.parametrize("prec,reals", [(F32, 18), (F32, 12), (F16, 12), (F16, 18)])
+@pytest.mark.parametrize("nrhs,slots", [(1, 0), (4, 3), (12, 0), (3, 2)])
+def test_row_streamed_kernel(dims, prec, reals, nrhs, slots):
+    """The row-streamed kernel (whole neighbour rows and their links copied into a ring of
+    shared-memory slots by bulk copies) against the oracle, for several slot counts and
+    right-hand-side counts; where the rows cannot be copied in 16-byte runs the launch is
+    an argument error."""
+    U = S.gauge_field(dims, 0.3, 18)
+    phis = np.stack([S.gaussian_spinor(dims, 400 + r) for r in range(nrhs)])
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, reals, prec)
+        ctx.set_launch(prec, nrhs, 0, 0, 1, 0, 4, slots)
+        if not rows_fit(dims, prec, reals, nrhs):
+            with pytest.raises(PLQError) as e:
+                gpu_hopping_full(ctx, phis if nrhs > 1 else phis[0], prec, nrhs)
+            assert e.value.status == plq.PLQ_ERR_ARG
+            return
+        got = gpu_hopping_full(ctx, phis if nrhs > 1 else phis[0], prec, nrhs).reshape(phis.shape)
+        assert ctx.device_status() == plq.PLQ_OK
+    for r in range(nrhs):
+        assert rel(got[r], W.hopping(U, phis[r])) <= TOL[prec], (r, rel(got[r], W.hopping(U, phis[r])))
+
+
+@pytest.mark.parametrize("prec,reals", [(F32, 18), (F16, 12)])
+def test_row_streamed_wilson_and_twisted_epilogues(prec, reals):
+    """The operator epilogues (Wilson M = 1 - kappa H, twisted mass) in the row-streamed
+    launch, against the oracle."""
+    dims = (8, 8, 4, 4)
+    U, phi = S.gauge_and_spinor(dims, 0.3, 19)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, reals, prec)
+        ctx.set_launch(prec, 1, 0, 0, 1, 0, 4, 0)
+        full = ctx.to_device(phi, prec)
+        out = ctx.empty_full(prec)
+        ctx.wilson_apply(out, full, 0.12, prec)
+        assert rel(ctx.to_host(out, prec), W.wilson(U, phi, 0.12)) <= TOL[prec]
+        ctx.twisted_apply(out, full, 0.12, 0.05, prec)
+        assert rel(ctx.to_host(out, prec), W.twisted(U, phi, 0.12, 0.05)) <= TOL[prec]
+
+
+def test_row_streamed_wait_limit_reports_timeout():
+    """Every wait of the row-streamed kernel is bounded: with a limit of one clock cycle
+    its first wait for a shared-memory copy gives up, the kernel records PLQ_ERR_TIMEOUT
+    in the context's status word and returns (no fault, no hang); with the default limit
+    restored the same context computes the right result."""
+    dims = (8, 8, 8, 8)
+    n = 4
+    U = S.gauge_field(dims, 0.3, 20)
+    phis = np.stack([S.gaussian_spinor(dims, 500 + r) for r in range(n)])
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F32)
+        ctx.set_launch(F32, n, 0, 0, 1, 0, 4, 3)
+        ctx.set_wait_limit(1e-12)
+        gpu_hopping_full(ctx, phis, F32, n)
+        assert ctx.device_status(clear=True) == plq.PLQ_ERR_TIMEOUT
+        assert ctx.device_status() == plq.PLQ_OK
+        ctx.set_wait_limit(5.0)
+        got = gpu_hopping_full(ctx, phis, F32, n).reshape(phis.shape)
+        assert ctx.device_status() == plq.PLQ_OK
+    for r in range(n):
+        assert rel(got[r], W.hopping(U, phis[r])) <= TOL[F32]

@@ -198,7 +198,7 @@ def test_fp16_inner_point_source_long_lattice(method):
         assert res <= 1e-10, (r, res, infos[r].as_dict())
 
 
-@pytest.mark.parametrize("tile,sm", [(2, 0), (4, 0), (1, 1), (2, 1), (1, 2), (1, 3)])
+@pytest.mark.parametrize("tile,sm", [(2, 0), (4, 0), (1, 1), (2, 1), (1, 2), (1, 3), (1, 4)])
 def test_multi_rhs_cg_with_rhs_tiles(tile, sm):
     dims = (8, 4, 4, 8)
     kappa = 0.12
@@ -376,3 +376,156 @@ def test_solver_graph_follows_gauge_and_launch_changes():
             ctx.cg_solve(x, bd, kappa, inner_prec=F32)
             res = oracle_residual(U, b, ctx.to_host(x, F64), kappa)
             assert res <= 1e-10, (reals, kappa, block, res)
+
+
+@pytest.mark.parametrize("method,inner,tile,sm", [("cg", F32, 1, 0), ("cg", F16, 1, 1), ("cg", F32, 2, 0),
+                                                  ("bicgstab", F32, 1, 0), ("cg", F64, 1, 0)])
+def test_solves_are_bitwise_reproducible(method, inner, tile, sm):
+    """Every reduction of the solvers (fused operator epilogues and vector kernels) adds
+    FP64 partial sums in a fixed order, so two identical multi-right-hand-side solves in
+    the same launch configuration return bit-identical iteration counts, residuals and
+    solutions; the residuals also pass the oracle's check."""
+    dims = (16, 8, 8, 8)
+    kappa = 0.12
+    n = 6
+    U = S.gauge_field(dims, 0.3, 13)
+    srcs = np.stack([S.gaussian_spinor(dims, 60 + r) for r in range(n)])
+    runs = []
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        if inner != F64:
+            ctx.gauge_upload(U, 12, inner)
+            ctx.set_launch(inner, n, 0, 0, 1 if n % tile else tile, 0, sm)
+        bd = ctx.to_device(srcs, F64, n)
+        fn = ctx.cg_solve_multi if method == "cg" else ctx.bicgstab_solve_multi
+        for _ in range(2):
+            x = ctx.empty_full(F64, n)
+            x.zero_()
+            infos = fn(x, bd, kappa, n, inner_prec=inner)
+            runs.append((ctx.to_host(x, F64, n), [(i.iterations, i.n_reliable, i.true_rel_residual) for i in infos]))
+    (x0, i0), (x1, i1) = runs
+    assert i0 == i1
+    assert np.array_equal(x0.view(np.float64), x1.view(np.float64))
+    xs = x0.reshape((n,) + srcs.shape[1:])
+    for r in range(n):
+        assert oracle_residual(U, srcs[r], xs[r], kappa) <= 1e-10
+
+
+def _batch(n=4, seed_shift=0):
+    specs = S.batch_solve_specs(n=n, sizes=((8, 4, 4, 4), (16, 8, 8, 8), (10, 4, 6, 8)))
+    ctxs, xs, bs, Us, srcs = [], [], [], [], []
+    for sp in specs:
+        U = S.gauge_field(sp["dims"], sp["eps"], sp["seed"])
+        ctx = Context(sp["dims"])
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        ctxs.append(ctx)
+        xs.append(ctx.empty_full(F64))
+        Us.append(U)
+    return specs, ctxs, xs, Us
+
+
+def _check_batch(specs, ctxs, xs, Us, srcs, infos):
+    for k, sp in enumerate(specs):
+        x = ctxs[k].to_host(xs[k], F64)
+        res = oracle_residual(Us[k], srcs[k], x, sp["kappa"])
+        assert res <= 1e-10, (k, res, infos[k].as_dict())
+
+
+def test_batched_graph_is_reused_for_new_sources():
+    """The second persistent launch with the same first context and shape replays the
+    instantiated graph: with the same sources it returns bit-identical solutions, with
+    new sources and kappas it solves the new systems (the descriptors are rewritten
+    before every launch)."""
+    from paper_1405_0700_gb300 import plq as P
+
+    specs, ctxs, xs, Us = _batch()
+    kappas = [sp["kappa"] for sp in specs]
+    srcs = [S.gaussian_spinor(sp["dims"], 700 + k) for k, sp in enumerate(specs)]
+    bs = [c.to_device(b, F64) for c, b in zip(ctxs, srcs)]
+    infos, b1 = P.cg_solve_batched(ctxs, xs, bs, kappas, inner_prec=F32)
+    first = [c.to_host(x, F64) for c, x in zip(ctxs, xs)]
+    _check_batch(specs, ctxs, xs, Us, srcs, infos)
+    infos2, b2 = P.cg_solve_batched(ctxs, xs, bs, kappas, inner_prec=F32)
+    assert b1["graph_captured"] == 1 and b2["graph_reused"] == 1 and b1["grid"] == b2["grid"]
+    for c, x, f in zip(ctxs, xs, first):
+        assert np.array_equal(c.to_host(x, F64), f)
+    assert [i.iterations for i in infos2] == [i.iterations for i in infos]
+    srcs3 = [S.gaussian_spinor(sp["dims"], 800 + k) for k, sp in enumerate(specs)]
+    bs3 = [c.to_device(b, F64) for c, b in zip(ctxs, srcs3)]
+    kappas3 = [k * 0.98 for k in kappas]
+    specs3 = [dict(sp, kappa=k) for sp, k in zip(specs, kappas3)]
+    infos3, b3 = P.cg_solve_batched(ctxs, xs, bs3, kappas3, inner_prec=F32)
+    assert b3["graph_reused"] == 1
+    _check_batch(specs3, ctxs, xs, Us, srcs3, infos3)
+    for c in ctxs:
+        c.close()
+
+
+@pytest.mark.parametrize("block,bps", [(64, 0), (128, 2), (192, 0), (256, 1)])
+def test_batched_launch_shapes(block, bps):
+    """Every launch shape of the persistent kernel (threads per block and resident blocks
+    per SM) solves the batch; the report names the shape used."""
+    from paper_1405_0700_gb300 import plq as P
+
+    specs, ctxs, xs, Us = _batch()
+    srcs = [S.gaussian_spinor(sp["dims"], 900 + k) for k, sp in enumerate(specs)]
+    bs = [c.to_device(b, F64) for c, b in zip(ctxs, srcs)]
+    P.set_batched_launch(ctxs[0], block, bps)
+    infos, bi = P.cg_solve_batched(ctxs, xs, bs, [sp["kappa"] for sp in specs], inner_prec=F32)
+    assert bi["block"] == block and (bps == 0 or bi["blocks_per_sm"] == bps)
+    _check_batch(specs, ctxs, xs, Us, srcs, infos)
+    with pytest.raises(PLQError):
+        P.set_batched_launch(ctxs[0], 100, 0)
+    for c in ctxs:
+        c.close()
+
+
+def test_batched_autotune_and_cache(tmp_path):
+    """The launch-shape tuner times the shapes on the batch, keeps the fastest in the
+    first context and writes it to the cache file, which a second tuning call reads
+    back without timing; solves with the chosen shape stay correct."""
+    from paper_1405_0700_gb300 import plq as P
+
+    specs, ctxs, xs, Us = _batch()
+    kappas = [sp["kappa"] for sp in specs]
+    srcs = [S.gaussian_spinor(sp["dims"], 1000 + k) for k, sp in enumerate(specs)]
+    bs = [c.to_device(b, F64) for c, b in zip(ctxs, srcs)]
+    path = str(tmp_path / "tune.txt")
+    best = P.autotune_batched(ctxs, xs, bs, kappas, inner_prec=F32, cache_path=path)
+    assert best["block"] in (64, 128, 192, 256) and best["seconds"] > 0
+    line = open(path).read().strip().split()
+    assert len(line) == 4 and int(line[1]) == best["block"]
+    again = P.autotune_batched(ctxs, xs, bs, kappas, inner_prec=F32, cache_path=path)
+    assert again["block"] == best["block"] and again["grid"] == 0  # from the cache: nothing ran
+    infos, bi = P.cg_solve_batched(ctxs, xs, bs, kappas, inner_prec=F32)
+    assert bi["block"] == best["block"]
+    _check_batch(specs, ctxs, xs, Us, srcs, infos)
+    for c in ctxs:
+        c.close()
+
+
+@pytest.mark.parametrize("sm", [0, 1, 4])
+@pytest.mark.parametrize("n", [12, 5])
+def test_multi_rhs_identical_sources_iterate_alike(sm, n):
+    """n copies of one source solved together must each take the iterations of the single
+    solve: every right-hand side's reductions (operator epilogues and vector kernels, whose
+    blocks for n = 12 or 5 end in a partial warp) must see all of its elements."""
+    dims = (16, 8, 8, 8)
+    kappa = 0.12
+    U, b = S.gauge_and_spinor(dims, 0.3, 21)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        bd1 = ctx.to_device(b, F64)
+        x1 = ctx.empty_full(F64)
+        single = ctx.cg_solve(x1, bd1, kappa, inner_prec=F32)
+        ctx.set_launch(F32, n, 0, 0, 1, 0, sm)
+        bd = ctx.to_device(np.stack([b] * n), F64, n)
+        x = ctx.empty_full(F64, n)
+        infos = ctx.cg_solve_multi(x, bd, kappa, n, inner_prec=F32)
+        xs = ctx.to_host(x, F64, n).reshape((n,) + b.shape)
+    its = [i.iterations for i in infos]
+    assert max(its) - min(its) <= 1 and abs(its[0] - single.iterations) <= 1, (its, single.iterations)
+    for r in range(n):
+        assert oracle_residual(U, b, xs[r], kappa) <= 1e-10

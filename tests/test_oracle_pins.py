@@ -88,8 +88,9 @@ def test_brute_force_dense(dims):
     assert brute_force_error(W.hopping, U) < 1e-14
 
 
-@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 2, 2, 2), (2, 4, 2, 2), (4, 4, 2, 2)])
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 2, 2, 2), (2, 4, 2, 2), (4, 4, 2, 2), (4, 4, 4, 4)])
 def test_free_field_plane_wave_spectrum(dims):
+    # the whole dense spectrum (3072 eigenvalues on 4^4) as a multiset against the closed form
     assert free_field_spectrum_error(W.hopping, dims, kappa=0.12) < 1e-12
 
 

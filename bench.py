@@ -62,7 +62,8 @@ def log(*a):
 
 
 KERNEL_SOURCES = ["paper_1405_0700_gb300/csrc/plq_hop_impl.cuh", "paper_1405_0700_gb300/csrc/plq_fields.cuh",
-                  "paper_1405_0700_gb300/csrc/plq_internal.cuh", "paper_1405_0700_gb300/csrc/plq_hop_f32_18.cu"]
+                  "paper_1405_0700_gb300/csrc/plq_internal.cuh", "paper_1405_0700_gb300/csrc/plq_fastdiv.h",
+                  "paper_1405_0700_gb300/csrc/plq_hop_f32_18.cu"]
 
 
 def kernel_source_hash():

@@ -473,9 +473,10 @@ typedef struct {
                              memory; 2 / 3 the same plus the neighbour spinors of the next
                              1 / 2 directions copied ahead into per-thread shared slots;
                              any nrhs (FP32/FP16): 4 row-streamed kernel, whole rows of
-                             neighbour spinors and links copied into a ring of shared-
-                             memory slots by bulk (TMA) copies; sites_per_thread is then
-                             the number of slots (0: as many as fit)                   */
+                             neighbour spinors copied into a ring of shared-memory slots
+                             by bulk (TMA) copies, sites_per_thread then being the number
+                             of slots (0: as many as fit); set by plq_set_launch only
+                             (the tuner does not time it: slower on GB300)             */
     double us_per_launch; /* measured time of one half-lattice application                 */
     int from_cache;       /* 1 if the choice came from the cache file                      */
     int candidates;       /* configurations timed                                          */
@@ -515,8 +516,8 @@ PLQ_API plq_status plq_autotune(plq_ctx *ctx, int prec, int nrhs, const char *ca
  * cannot launch makes the operator calls return PLQ_ERR_ARG), index_mode 0 or 1,
  * rhs_tile 1, 2 or 4 (dividing nrhs), z_chunk 0 or a divisor of Lz and
  * smem_links 0..4 (1..3: nrhs > 1, FP32/FP16; 4: FP32/FP16, needs nrhs x Lx/2
- * <= 512 and 16-byte row runs, else the operator calls return PLQ_ERR_ARG;
- * with 1, rhs_tile 1 or 2; with 2, 3 or 4,
+ * <= 512 and, for FP16 storage, site-norm runs of 16-byte multiples, else the
+ * operator calls return PLQ_ERR_ARG; with 1, rhs_tile 1 or 2; with 2, 3 or 4,
  * rhs_tile 1) and sites_per_thread 0..64, as above. */
 PLQ_API plq_status plq_set_launch(plq_ctx *ctx, int prec, int nrhs, int block, int index_mode, int rhs_tile,
                                   int z_chunk, int smem_links, int sites_per_thread);

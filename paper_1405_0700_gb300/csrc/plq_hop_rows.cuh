@@ -7,22 +7,20 @@
 // its sites have consecutive checkerboard indices, so in every packed plane
 // the row's n right-hand sides are one contiguous run of (Lx/2)*n elements.
 // A block owns one output row at a time (threads = n right-hand sides x Lx/2
-// sites) and consumes it in 7 stages, each one input row plus the link rows
-// its directions need:
+// sites) and consumes it in 7 stages, each one input row:
 //   stage 0  the row itself (same y, z, t): neighbours +x and -x of every site
-//            (the site to the right or left within the row, by row parity),
-//            links U_x at the output row and at the input row (for U_x(x-x)^dag)
-//   stage 1  row y+1 (periodic), links U_y at the output row
-//   stage 2  row y-1,           links U_y at that input row (daggered)
-//   stage 3,4  rows z+1, z-1 with U_z;  stage 5,6  rows t+1, t-1 with U_t
-//            (the time-boundary sign applies when the row wraps in t).
-// One thread issues each stage as a handful of 1-D bulk copies
+//            (the site to the right or left within the row, by row parity)
+//   stage 1, 2  rows y+1, y-1 (periodic);  stage 3, 4  rows z+1, z-1
+//   stage 5, 6  rows t+1, t-1 (the time-boundary sign applies when the row
+//            wraps in t).
+// One thread issues each stage as one 1-D bulk copy per spinor plane
 // (cp.async.bulk, completion counted in bytes on an mbarrier) several stages
-// ahead; the block waits on the stage's barrier, computes the directions of
-// the stage for its (site, right-hand side) elements from shared memory, and
-// the slot of the previous stage is refilled.  The loads in flight therefore
-// take no registers, and the +-x (and partly +-y) neighbours are read once
-// per row instead of once per site.
+// ahead; the block waits on the stage's barrier and computes the directions
+// of the stage for its (site, right-hand side) elements with the neighbour
+// read from shared memory and the link read from global memory (the n
+// threads of a site share each link request).  The spinor loads in flight
+// take no registers, and the +-x neighbours are read once per row instead of
+// once per site.
 //
 // Every wait on a barrier is bounded (HopArgs::spin_limit clock cycles); a
 // block that runs out records PLQ_ERR_TIMEOUT in *HopArgs::kstatus, waits
@@ -79,115 +77,23 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  : "memory");
 }
 
-// Per-site bytes of the planes of one (parity, mu) link block: wide planes of
-// 16 bytes, then at most one narrow plane.
-template <int P, int R>
-struct LinkPlanes;
-template <>
-struct LinkPlanes<PLQ_F32, 18> {
-    static constexpr int wide = 4, narrow = 8;
-};
-template <>
-struct LinkPlanes<PLQ_F32, 12> {
-    static constexpr int wide = 3, narrow = 0;
-};
-template <>
-struct LinkPlanes<PLQ_F16, 18> {
-    static constexpr int wide = 2, narrow = 4;
-};
-template <>
-struct LinkPlanes<PLQ_F16, 12> {
-    static constexpr int wide = 1, narrow = 8;
-};
-
-template <int P, int R>
-__host__ __device__ constexpr int link_site_bytes_c() {
-    return 16 * LinkPlanes<P, R>::wide + LinkPlanes<P, R>::narrow;
-}
-
-// Shared-memory bytes of one row of spinors (n right-hand sides) and of one
-// row of links, each rounded up to 16.
+// Shared-memory bytes of one row of spinors (n right-hand sides), rounded up
+// to 16: one slot of the ring.
 template <int P>
 __host__ __device__ inline size_t rows_spinor_bytes(int Lxh, int n) {
     const size_t e = (size_t)Lxh * n;
     return ((e * 16 * spinor_planes<P>() + (P == PLQ_F16 ? e * 4 : 0)) + 15) & ~(size_t)15;
 }
 template <int P, int R>
-__host__ __device__ inline size_t rows_link_bytes(int Lxh) {
-    return ((size_t)Lxh * link_site_bytes_c<P, R>() + 15) & ~(size_t)15;
-}
-template <int P, int R>
 __host__ __device__ inline size_t rows_slot_bytes(int Lxh, int n) {
-    return rows_spinor_bytes<P>(Lxh, n) + 2 * rows_link_bytes<P, R>(Lxh);
+    return rows_spinor_bytes<P>(Lxh, n);
 }
 
-// The row layout can be copied with 16-byte bulk copies (every run a
-// multiple of 16 bytes starting on a 16-byte boundary).
+// The row's runs can be copied with 16-byte bulk copies (FP16 storage: the
+// run of 4-byte site norms must be a multiple of 16 bytes).
 template <int P, int R>
 inline bool rows_copyable(int Lxh, int n) {
-    if (P == PLQ_F16 && ((long long)Lxh * n) % 4 != 0) return false;  // norm runs of 4-byte floats
-    constexpr int nb = LinkPlanes<P, R>::narrow;
-    if (nb > 0 && ((long long)Lxh * nb) % 16 != 0) return false;
-    return true;
-}
-
-// Link of one site from a row of link planes in shared memory (the global
-// plane layout with the row's Lx/2 sites in place of Vh).
-template <int P, int R>
-__device__ __forceinline__ void row_link(const unsigned char *row, int Lxh, int xh, cx<RealOf<P>> u[3][3]) {
-    if constexpr (P == PLQ_F32) {
-        const float4 *w = reinterpret_cast<const float4 *>(row) + xh;
-        if constexpr (R == 18) {
-            cx<float> c[9];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float4 t = w[(size_t)k * Lxh];
-                c[2 * k] = {t.x, t.y};
-                c[2 * k + 1] = {t.z, t.w};
-            }
-            const float2 t = reinterpret_cast<const float2 *>(row + (size_t)4 * Lxh * 16)[xh];
-            c[8] = {t.x, t.y};
-#pragma unroll
-            for (int k = 0; k < 9; ++k) u[k / 3][k % 3] = c[k];
-        } else {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float4 t = w[(size_t)k * Lxh];
-                u[(2 * k) / 3][(2 * k) % 3] = {t.x, t.y};
-                u[(2 * k + 1) / 3][(2 * k + 1) % 3] = {t.z, t.w};
-            }
-            reconstruct_row2(u);
-        }
-    } else {
-        const uint4 *w = reinterpret_cast<const uint4 *>(row) + xh;
-        if constexpr (R == 18) {
-            cx<float> c[9];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const uint4 t = w[(size_t)k * Lxh];
-                const float2 a = h2f(t.x), b = h2f(t.y), d = h2f(t.z), e = h2f(t.w);
-                c[4 * k] = {a.x, a.y};
-                c[4 * k + 1] = {b.x, b.y};
-                c[4 * k + 2] = {d.x, d.y};
-                c[4 * k + 3] = {e.x, e.y};
-            }
-            const float2 t = h2f(reinterpret_cast<const unsigned *>(row + (size_t)2 * Lxh * 16)[xh]);
-            c[8] = {t.x, t.y};
-#pragma unroll
-            for (int k = 0; k < 9; ++k) u[k / 3][k % 3] = c[k];
-        } else {
-            const uint4 t = w[0];
-            const uint2 q = reinterpret_cast<const uint2 *>(row + (size_t)Lxh * 16)[xh];
-            const float2 a = h2f(t.x), b = h2f(t.y), d = h2f(t.z), e = h2f(t.w), f = h2f(q.x), g = h2f(q.y);
-            u[0][0] = {a.x, a.y};
-            u[0][1] = {b.x, b.y};
-            u[0][2] = {d.x, d.y};
-            u[1][0] = {e.x, e.y};
-            u[1][1] = {f.x, f.y};
-            u[1][2] = {g.x, g.y};
-            reconstruct_row2(u);
-        }
-    }
+    return !(P == PLQ_F16 && ((long long)Lxh * n) % 4 != 0);
 }
 
 // Neighbour spinor (element xh, right-hand side r) from a spinor row in shared
@@ -223,16 +129,16 @@ __device__ __forceinline__ float row_spinor(const unsigned char *row, int Lxh, i
 // One direction: project the neighbour with (1 + S gamma_MU), scale (FP16 norm,
 // time-boundary sign), multiply by U (BACK = false) or U^dagger, accumulate.
 template <int P, int R, int MU, int S, bool BACK>
-__device__ __forceinline__ void rows_dir(const unsigned char *sp, const unsigned char *lk, int Lxh, int n, int xn,
-                                         int xl, int r, float sign, cx<float> acc[12]) {
+__device__ __forceinline__ void rows_dir(const unsigned char *sp, const void *lblk, int Vh, int li, int Lxh, int n,
+                                         int xn, int r, float sign, cx<float> acc[12]) {
     cx<float> phi[12], h[6], uh[6], u[3][3];
+    Link<P, R>::load(lblk, Vh, li, u);  // from global memory; the n threads of a site share the request
     const float sc = row_spinor<P>(sp, Lxh, n, xn, r, phi) * sign;
     project<MU, S>(phi, h);
     if (P == PLQ_F16 || sign != 1.f) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) h[k] = {sc * h[k].re, sc * h[k].im};
     }
-    row_link<P, R>(lk, Lxh, xl, u);
     if constexpr (BACK) su3_dag_mul(u, h, uh);
     else su3_mul(u, h, uh);
     reconstruct<MU, S>(acc, uh);
@@ -253,8 +159,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) hop_rows_kernel(const HopArgs 
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nrows = L.Vh / Lxh;
     const size_t stride = (size_t)L.Vh * n;  // elements of one spinor plane
-    const size_t sp_bytes = rows_spinor_bytes<P>(Lxh, n), lk_bytes = rows_link_bytes<P, R>(Lxh);
-    const size_t slot_bytes = sp_bytes + 2 * lk_bytes;
+    const size_t slot_bytes = rows_spinor_bytes<P>(Lxh, n);
     const int par = a.out_parity;
     const char *gbase = static_cast<const char *>(a.gauge);
     const unsigned char *in = static_cast<const unsigned char *>(a.in);
@@ -289,18 +194,6 @@ __global__ void __launch_bounds__(kRowThreads, 1) hop_rows_kernel(const HopArgs 
         *lb_row = ro;
     };
 
-    auto copy_link_row = [&](unsigned char *dst, int blk, int row, unsigned long long *bar) {
-        const unsigned char *b = reinterpret_cast<const unsigned char *>(gbase) + (size_t)blk * a.gblock;
-        constexpr int W = LinkPlanes<P, R>::wide, NB = LinkPlanes<P, R>::narrow;
-#pragma unroll
-        for (int k = 0; k < W; ++k)
-            bulk_g2s(dst + (size_t)k * Lxh * 16, b + ((size_t)k * L.Vh + (size_t)row * Lxh) * 16, (unsigned)Lxh * 16,
-                     bar);
-        if constexpr (NB > 0)
-            bulk_g2s(dst + (size_t)W * Lxh * 16, b + (size_t)W * L.Vh * 16 + (size_t)row * Lxh * NB,
-                     (unsigned)(Lxh * NB), bar);
-    };
-
     auto issue = [&](long long g) {
         int ri, la_blk, la_row, lb_blk, lb_row, ro, t;
         stage_rows(g, &ri, &la_blk, &la_row, &lb_blk, &lb_row, &ro, &t);
@@ -309,8 +202,8 @@ __global__ void __launch_bounds__(kRowThreads, 1) hop_rows_kernel(const HopArgs 
         const int s = (int)(g % 7);
         const size_t e0 = (size_t)ri * Lxh * n, ne = (size_t)Lxh * n;
         constexpr int NP = spinor_planes<P>();
-        const unsigned lkb = (unsigned)(Lxh * link_site_bytes_c<P, R>());
-        const unsigned bytes = (unsigned)(ne * 16 * NP + (P == PLQ_F16 ? ne * 4 : 0)) + lkb * (s == 0 ? 2u : 1u);
+        const unsigned bytes = (unsigned)(ne * 16 * NP + (P == PLQ_F16 ? ne * 4 : 0));
+        (void)s;
         mbar_arrive_expect_tx(&bars[slot], bytes);
 #pragma unroll
         for (int q = 0; q < NP; ++q)
@@ -318,8 +211,6 @@ __global__ void __launch_bounds__(kRowThreads, 1) hop_rows_kernel(const HopArgs 
         if constexpr (P == PLQ_F16)
             bulk_g2s(base + (size_t)NP * ne * 16, in + (size_t)NP * stride * 16 + e0 * 4, (unsigned)(ne * 4),
                      &bars[slot]);
-        copy_link_row(base + sp_bytes, la_blk, la_row, &bars[slot]);
-        if (s == 0) copy_link_row(base + sp_bytes + lk_bytes, lb_blk, lb_row, &bars[slot]);
     };
 
     if (tid == 0) {
@@ -352,7 +243,6 @@ __global__ void __launch_bounds__(kRowThreads, 1) hop_rows_kernel(const HopArgs 
             issue(g - 1 + nslot);
         }
         const unsigned char *base = rows_smem + (size_t)slot * slot_bytes;
-        const unsigned char *la = base + sp_bytes, *lb = base + sp_bytes + lk_bytes;
         const int s = (int)(g % 7);
         int ri, la_blk, la_row, lb_blk, lb_row, ro, t;
         stage_rows(g, &ri, &la_blk, &la_row, &lb_blk, &lb_row, &ro, &t);
@@ -360,26 +250,29 @@ __global__ void __launch_bounds__(kRowThreads, 1) hop_rows_kernel(const HopArgs 
         fd_divmod(fd_divmod((unsigned)ro, L.div_y, &yy), L.div_z, &zz);
         const int o = (par + (int)yy + (int)zz + t) & 1;  // x = 2 xh + o on the output row
         if (r < n && xh < Lxh) {
+            const void *la = gbase + (size_t)la_blk * a.gblock;
+            const int lrow = la_row * Lxh;
             switch (s) {
             case 0: {
                 const int xp = o == 0 ? xh : (xh + 1 == Lxh ? 0 : xh + 1);
                 const int xm = o == 1 ? xh : (xh == 0 ? Lxh - 1 : xh - 1);
-                rows_dir<P, R, 1, SF, false>(base, la, Lxh, n, xp, xh, r, 1.f, acc);
-                rows_dir<P, R, 1, SB, true>(base, lb, Lxh, n, xm, xm, r, 1.f, acc);
+                const void *lb = gbase + (size_t)lb_blk * a.gblock;
+                rows_dir<P, R, 1, SF, false>(base, la, L.Vh, lrow + xh, Lxh, n, xp, r, 1.f, acc);
+                rows_dir<P, R, 1, SB, true>(base, lb, L.Vh, lb_row * Lxh + xm, Lxh, n, xm, r, 1.f, acc);
                 break;
             }
-            case 1: rows_dir<P, R, 2, SF, false>(base, la, Lxh, n, xh, xh, r, 1.f, acc); break;
-            case 2: rows_dir<P, R, 2, SB, true>(base, la, Lxh, n, xh, xh, r, 1.f, acc); break;
-            case 3: rows_dir<P, R, 3, SF, false>(base, la, Lxh, n, xh, xh, r, 1.f, acc); break;
-            case 4: rows_dir<P, R, 3, SB, true>(base, la, Lxh, n, xh, xh, r, 1.f, acc); break;
+            case 1: rows_dir<P, R, 2, SF, false>(base, la, L.Vh, lrow + xh, Lxh, n, xh, r, 1.f, acc); break;
+            case 2: rows_dir<P, R, 2, SB, true>(base, la, L.Vh, lrow + xh, Lxh, n, xh, r, 1.f, acc); break;
+            case 3: rows_dir<P, R, 3, SF, false>(base, la, L.Vh, lrow + xh, Lxh, n, xh, r, 1.f, acc); break;
+            case 4: rows_dir<P, R, 3, SB, true>(base, la, L.Vh, lrow + xh, Lxh, n, xh, r, 1.f, acc); break;
             case 5: {
                 const float sg = (t == L.L[0] - 1 && L.t_bc < 0) ? -1.f : 1.f;
-                rows_dir<P, R, 0, SF, false>(base, la, Lxh, n, xh, xh, r, sg, acc);
+                rows_dir<P, R, 0, SF, false>(base, la, L.Vh, lrow + xh, Lxh, n, xh, r, sg, acc);
                 break;
             }
             default: {
                 const float sg = (t == 0 && L.t_bc < 0) ? -1.f : 1.f;
-                rows_dir<P, R, 0, SB, true>(base, la, Lxh, n, xh, xh, r, sg, acc);
+                rows_dir<P, R, 0, SB, true>(base, la, L.Vh, lrow + xh, Lxh, n, xh, r, sg, acc);
                 break;
             }
             }

@@ -233,28 +233,10 @@ extern "C" plq_status plq_autotune(plq_ctx *c, int prec, int nrhs, const char *c
             }
         }
     }
-    // the row-streamed kernel (its block is fixed by nrhs and Lx/2; the
-    // sites-per-thread field selects how many shared-memory slots it rings
-    // through, 0 = as many as fit)
-    if (prec != PLQ_F64) {
-        for (int k : {0, 3, 4, 6}) {
-            if (st != PLQ_OK) break;
-            TuneEntry t;
-            t.block = 0;
-            t.smem_links = 4;
-            t.spt = k;
-            float us = -1.f;
-            st = time_cfg(t, &us);
-            if (st == PLQ_OK && us >= 0.f && us < best.us) {
-                t.us = us;
-                best = t;
-            }
-        }
-    }
     // sites per thread: a grid sized for k sites (site blocks) per thread
     // against the one-wave grid of the sweep above
     for (int k : {1, 2, 4, 8}) {
-        if (st != PLQ_OK || best.smem_links == 4) break;
+        if (st != PLQ_OK) break;
         TuneEntry t = best;
         t.spt = k;
         float us = -1.f;

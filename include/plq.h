@@ -96,7 +96,9 @@ enum {
     PLQ_ERR_BREAKDOWN = 5,     /* Krylov breakdown (rho or omega vanished)         */
     PLQ_ERR_NAN = 6,           /* a NaN or Inf appeared in a solver scalar         */
     PLQ_ERR_TIMEOUT = 7,       /* a device-side wait ran out of its spin limit     */
-    PLQ_ERR_STATE = 8          /* call out of order (e.g. no gauge field uploaded) */
+    PLQ_ERR_STATE = 8,         /* call out of order (e.g. no gauge field uploaded) */
+    PLQ_ERR_BOUNDS = 9         /* debug build (PLQ_DEBUG): a device bounds guard found an
+                                  index out of range (recorded, access redirected)  */
 };
 
 /* Storage precisions of packed fields.  PLQ_F32 and PLQ_F16 compute in FP32;
@@ -186,8 +188,10 @@ PLQ_API plq_status plq_set_wait_limit(plq_ctx *ctx, double seconds);
 /* Defined by: paper silent (failure detection of this library's kernels).
  *
  * Reads the context's device status word (synchronising the device): PLQ_OK,
- * or the error a kernel recorded (PLQ_ERR_TIMEOUT: a bounded wait gave up),
- * which is then also the return value.  clear != 0 resets the word. */
+ * or the error a kernel recorded (PLQ_ERR_TIMEOUT: a bounded wait gave up;
+ * PLQ_ERR_BOUNDS: in a library built with PLQ_DEBUG, a device bounds guard
+ * found an out-of-range index), which is then also the return value.
+ * clear != 0 resets the word. */
 PLQ_API plq_status plq_device_status(plq_ctx *ctx, int clear);
 
 /* Number of sites of one parity, Vh.

@@ -18,6 +18,11 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libplq.so")
 INCLUDE = os.path.join(ROOT, "include")
+# The debug build: the same sources compiled with -DPLQ_DEBUG (device bounds
+# guards that record PLQ_ERR_BOUNDS in the context's status word instead of
+# accessing out of range), in its own object folder and library.
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libplq_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + [
@@ -46,16 +51,20 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose=False, jobs=None, extra_flags=()):
-    """Compile and link libplq.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, jobs=None, extra_flags=(), debug=False):
+    """Compile and link libplq.so (with debug=True: libplq_debug.so, the
+    PLQ_DEBUG build); returns its path."""
+    build_dir, lib_path = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if debug:
+        extra_flags = tuple(extra_flags) + ("-DPLQ_DEBUG",)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdrs = _headers()
     nv = nvcc()
     jobs_todo = []
     objs = []
     for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if _stale(obj, [src] + hdrs):
             jobs_todo.append((src, obj))
@@ -74,14 +83,14 @@ def build(verbose=False, jobs=None, extra_flags=()):
         for src, err in ex.map(compile_one, jobs_todo):
             if verbose:
                 print("compiled", os.path.basename(src), err.strip())
-    if _stale(LIB, objs) or jobs_todo:
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if _stale(lib_path, objs) or jobs_todo:
+        tmp = lib_path + ".tmp%d" % os.getpid()
         cmd = [nv] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -155,6 +155,10 @@ extern "C" plq_status plq_cg_solve_batched(plq_ctx **ctxs, int n, void **x, cons
             stt = cuda_error(e, "batched CG kernel");
             break;
         }
+        if (status_word == PLQ_ERR_BOUNDS) {
+            stt = set_error(PLQ_ERR_BOUNDS, "batched CG: a device bounds guard found an index out of range");
+            break;
+        }
         if (status_word != 0) {
             stt = set_error(PLQ_ERR_TIMEOUT, "batched CG: a grid barrier exceeded its wait limit");
             break;

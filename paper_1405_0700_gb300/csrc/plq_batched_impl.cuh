@@ -532,7 +532,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) batched_cg_kernel(BatchArgs a) {
         for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total; g += stride) {
             int s = 0;
             while (g >= prefix[s + 1]) ++s;
-            const int i = (int)(g - prefix[s]);
+            s = PLQ_GUARD(a.status, s, ns);
+            const int i = PLQ_GUARD(a.status, (int)(g - prefix[s]), a.sys[s].lat.Vh);
             const double v = run_site<PL, RL>(run[s].mode, a.sys[s], run[s], i);
             if (reduces(run[s].mode)) {
                 // warp-level sum when the whole warp works on one system

@@ -329,6 +329,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
             j = yl >> 1;
             flip = MU == 0 && cm == Lm - 1 && L.t_bc < 0;
         }
+        j = PLQ_GUARD(a.kstatus, j, L.Vh);
         cx<T> u[3][3];
         Link<P, R>::load(gbase + (size_t)(a.out_parity * 4 + MU) * a.gblock, L.Vh, i, u);
 #pragma unroll
@@ -347,6 +348,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &a, const SiteGeom &g, int
             j = yl >> 1;
             flip = MU == 0 && cm == 0 && L.t_bc < 0;
         }
+        j = PLQ_GUARD(a.kstatus, j, L.Vh);
         cx<T> u[3][3];
         Link<P, R>::load(gbase + (size_t)((1 - a.out_parity) * 4 + MU) * a.gblock, L.Vh, j, u);
 #pragma unroll
@@ -390,6 +392,7 @@ __device__ __forceinline__ void hop_body(const HopArgs &a) {
             const int w = rem - zi * plane;
             i = (t * a.lat.L[3] + c * zc + zi) * plane + w;
         }
+        i = PLQ_GUARD(a.kstatus, i, a.lat.Vh);
         bool all_frozen = a.st != nullptr;
 #pragma unroll
         for (int t = 0; t < RT; ++t) all_frozen = all_frozen && a.st[r0 + t].stop;
@@ -410,7 +413,7 @@ __device__ __forceinline__ void hop_body(const HopArgs &a) {
         for (int t = 0; t < RT; ++t) {
             const int rr = r0 + t;
             if (RT > 1 && a.st != nullptr && a.st[rr].stop) continue;
-            const long long idx = (long long)i * n + rr;
+            const long long idx = PLQ_GUARD(a.kstatus, (long long)i * n + rr, (long long)stride);
             if (a.nu_h != 0.0 || a.scale_h != 1.0) twist12(acc[t], (T)a.nu_h, (T)a.scale_h);
             if constexpr (EPI != EPI_PLAIN) {
                 cx<T> xv[12];
@@ -577,6 +580,7 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
                 const int zi = rem / plane;
                 i = (t * L.L[3] + c * zc + zi) * plane + (rem - zi * plane);
             }
+            i = PLQ_GUARD(a.kstatus, i, L.Vh);
             const SiteGeom g = site_geom(L, a.out_parity, i);
             const int st = mu == 0 ? L.L[1] * L.L[2] * L.L[3] : mu == 1 ? 1 : mu == 2 ? L.L[1] : L.L[1] * L.L[2];
             const int cm = g.c[mu], Lm = L.L[mu];
@@ -589,6 +593,7 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
                 j = ((cm == 0) ? g.lex + (Lm - 1) * st : g.lex - st) >> 1;
                 flip = mu == 0 && cm == 0 && L.t_bc < 0;
             }
+            j = PLQ_GUARD(a.kstatus, j, L.Vh);
             cx<T> u[3][3];
             Link<P, R>::load(gbase + (size_t)((back ? 1 - a.out_parity : a.out_parity) * 4 + mu) * a.gblock, L.Vh,
                              back ? j : i, u);
@@ -619,7 +624,7 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
         if (all_frozen) continue;
         // copy the neighbour spinor of direction d into slot b of this thread
         auto issue = [&](int d, int b) {
-            const size_t e = (size_t)sJ[k][d] * n + r0;
+            const size_t e = (size_t)PLQ_GUARD(a.kstatus, sJ[k][d], L.Vh) * n + r0;
             const uint4 *src = static_cast<const uint4 *>(a.in) + e;
 #pragma unroll
             for (int q = 0; q < NP; ++q) cp_async16(&sP[(size_t)(b * NP + q) * nthr + tid], src + q * stride);
@@ -639,7 +644,7 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
             for (int e = 0; e < 12; ++e) acc[t][e] = {T(0), T(0)};
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
-            const int j = sJ[k][d];
+            const int j = PLQ_GUARD(a.kstatus, sJ[k][d], L.Vh);
             const int mu = d >> 1;
             if constexpr (NB > 0) {
                 (void)j;
@@ -718,7 +723,7 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
         for (int t = 0; t < RT; ++t) {
             const int rr = r0 + t;
             if (a.st != nullptr && a.st[rr].stop) continue;
-            const long long idx = (long long)i * n + rr;
+            const long long idx = PLQ_GUARD(a.kstatus, (long long)i * n + rr, (long long)stride);
             if (a.nu_h != 0.0 || a.scale_h != 1.0) twist12(acc[t], (T)a.nu_h, (T)a.scale_h);
             if constexpr (EPI != EPI_PLAIN) {
                 cx<T> xv[12];

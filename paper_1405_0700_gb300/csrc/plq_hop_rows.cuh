@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) hop_rows_kernel(const HopArgs 
         else if (s == 4) nr = ro + (((int)z == 0 ? Lz - 1 : (int)z - 1) - (int)z) * Ly;
         else if (s == 5) nr = ro + ((t + 1 == T ? 0 : t + 1) - t) * Ly * Lz;
         else if (s == 6) nr = ro + ((t == 0 ? T - 1 : t - 1) - t) * Ly * Lz;
-        *ri = nr;
+        *ri = PLQ_GUARD(a.kstatus, nr, nrows);
         *ro_out = ro;
         *tcoord = t;
         const bool fwd = s == 0 || (s & 1);  // stages 0, 1, 3, 5 need U_mu(x) at the output row
@@ -250,12 +250,13 @@ __global__ void __launch_bounds__(kRowThreads, 1) hop_rows_kernel(const HopArgs 
         fd_divmod(fd_divmod((unsigned)ro, L.div_y, &yy), L.div_z, &zz);
         const int o = (par + (int)yy + (int)zz + t) & 1;  // x = 2 xh + o on the output row
         if (r < n && xh < Lxh) {
+            (void)PLQ_GUARD(a.kstatus, ro, nrows);
             const void *la = gbase + (size_t)la_blk * a.gblock;
             const int lrow = la_row * Lxh;
             switch (s) {
             case 0: {
-                const int xp = o == 0 ? xh : (xh + 1 == Lxh ? 0 : xh + 1);
-                const int xm = o == 1 ? xh : (xh == 0 ? Lxh - 1 : xh - 1);
+                const int xp = PLQ_GUARD(a.kstatus, o == 0 ? xh : (xh + 1 == Lxh ? 0 : xh + 1), Lxh);
+                const int xm = PLQ_GUARD(a.kstatus, o == 1 ? xh : (xh == 0 ? Lxh - 1 : xh - 1), Lxh);
                 const void *lb = gbase + (size_t)lb_blk * a.gblock;
                 rows_dir<P, R, 1, SF, false>(base, la, L.Vh, lrow + xh, Lxh, n, xp, r, 1.f, acc);
                 rows_dir<P, R, 1, SB, true>(base, lb, L.Vh, lb_row * Lxh + xm, Lxh, n, xm, r, 1.f, acc);
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(kRowThreads, 1) hop_rows_kernel(const HopArgs 
                 // the output element (site ro * Lx/2 + xh, right-hand side r)
                 const bool frozen = a.st != nullptr && a.st[r].stop;
                 if (!frozen) {
-                    const long long idx = ((long long)ro * Lxh + xh) * n + r;
+                    const long long idx = PLQ_GUARD(a.kstatus, ((long long)ro * Lxh + xh) * n + r, (long long)stride);
                     if (a.nu_h != 0.0 || a.scale_h != 1.0) twist12(acc, (T)a.nu_h, (T)a.scale_h);
                     if constexpr (EPI != EPI_PLAIN) {
                         cx<T> xv[12];

@@ -54,6 +54,23 @@ inline Lattice make_lattice(const int dims[4], int t_bc) {
 
 inline bool valid_prec(int p) { return p == PLQ_F64 || p == PLQ_F32 || p == PLQ_F16; }
 
+// Device bounds guards of the debug build (compiled with -DPLQ_DEBUG): an
+// index outside [0, n) is recorded as PLQ_ERR_BOUNDS in the status word (when
+// the kernel has one) and replaced by 0, so the access stays inside the
+// buffer and nothing faults.  In the normal build a guard is the index itself.
+#ifdef PLQ_DEBUG
+__device__ __forceinline__ long long plq_guard(int *status, long long v, long long n) {
+    if (v < 0 || v >= n) {
+        if (status) atomicCAS(status, 0, (int)PLQ_ERR_BOUNDS);
+        return 0;
+    }
+    return v;
+}
+#define PLQ_GUARD(status, v, n) ((decltype((v) + 0))::plq::plq_guard((status), (long long)(v), (long long)(n)))
+#else
+#define PLQ_GUARD(status, v, n) (v)
+#endif
+
 // bytes per site and right-hand side of a packed half field
 inline size_t spinor_site_bytes(int prec) { return prec == PLQ_F64 ? 192 : prec == PLQ_F32 ? 96 : 52; }
 

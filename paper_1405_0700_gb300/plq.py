@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libplq.so")
+# PLQ_LIBRARY may name another build of the same library (the PLQ_DEBUG build,
+# libplq_debug.so); there is no fallback if the file is missing.
+LIB_PATH = os.environ.get("PLQ_LIBRARY") or os.path.join(_HERE, "libplq.so")
 
 PLQ_OK = 0
 PLQ_ERR_ARG = 1
@@ -25,6 +27,7 @@ PLQ_ERR_BREAKDOWN = 5
 PLQ_ERR_NAN = 6
 PLQ_ERR_TIMEOUT = 7
 PLQ_ERR_STATE = 8
+PLQ_ERR_BOUNDS = 9
 
 F64, F32, F16, DF64 = 0, 1, 2, 3
 MAX_RHS = 12

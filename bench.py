@@ -601,6 +601,52 @@ def propagator_section(torch, local_rank, quick, fp64_rhs=4):
     return out
 
 
+def propsolve_only(args, torch, local_rank):
+    """One point-source multi-RHS mixed CG solve (--nrhs columns, FP32 inner
+    iterations with 12-real links, FP64 reliable updates, tol 1e-10) on --lattice
+    (default 32x32x32x64), timed after an identical warm-up solve; the timed solve
+    runs inside the NVTX range 'solve' so that a profiler can select its launches."""
+    from paper_1405_0700_gb300 import F32, F64, Context
+
+    dims = (64, 32, 32, 32)
+    if args.lattice:
+        lx, ly, lz, lt = (int(v) for v in args.lattice.lower().split("x"))
+        dims = (lt, lx, ly, lz)
+    n = max(1, min(args.nrhs, 12))
+    kappa = 0.121
+    U = S.gauge_field(dims, 0.25, 4)
+    V = S.volume(dims)
+    with Context(dims, device=local_rank) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        ctx.autotune(F32, n)
+        b = torch.zeros(n * V * 24, dtype=torch.float64, device=f"cuda:{local_rank}")
+        for r in range(n):  # source r: spin r // 3, colour r % 3 at the origin
+            b[r * V * 24 + 2 * r] = 1.0
+        bd = ctx.empty_full(F64, n)
+        ctx.pack_spinor(bd, b, F64, n)
+        del b
+        x = ctx.empty_full(F64, n)
+        runs = []
+        for k in range(2):
+            torch.cuda.synchronize()
+            if k == 1:
+                torch.cuda.nvtx.range_push("solve")
+            t0 = time.perf_counter()
+            infos = ctx.cg_solve_multi(x, bd, kappa, n, tol=1e-10, inner_prec=F32, maxit=3000, raise_on_error=False)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            if k == 1:
+                torch.cuda.nvtx.range_pop()
+            runs.append(el)
+    out = {"workload": "propsolve", "lattice": "x".join(map(str, dims[1:])) + "x" + str(dims[0]), "nrhs": n,
+           "kappa": kappa, "tol": 1e-10, "seconds": runs[1], "seconds_warm_up_solve": runs[0],
+           "seconds_per_rhs": runs[1] / n, "iterations": [i.iterations for i in infos],
+           "reliable_updates": infos[0].n_reliable, "hop_applications": infos[0].hop_applications,
+           "max_true_rel_residual": max(i.true_rel_residual for i in infos)}
+    print(json.dumps(out), flush=True)
+
+
 def operator_only(args, torch, local_rank):
     from paper_1405_0700_gb300 import Context
     from paper_1405_0700_gb300.plq import PREC_NAMES
@@ -780,8 +826,10 @@ def main():
                     help="point sources solved by plain FP64 CG as the propagator section's comparator")
     ap.add_argument("--quick", action="store_true", help="small lattices (smoke use only)")
     ap.add_argument("--source-hash", action="store_true", help="print the hash of the headline kernel's sources")
-    ap.add_argument("--workload", default="hop", choices=["hop", "propagator", "operator", "eigcg", "batch", "stream"],
-                    help="hop: the headline operator line (default); propagator: 48^3x96 with 12 point sources")
+    ap.add_argument("--workload", default="hop",
+                    choices=["hop", "propagator", "operator", "eigcg", "batch", "stream", "propsolve"],
+                    help="hop: the headline operator line (default); propagator: 48^3x96 with 12 point sources; "
+                         "propsolve: one multi-RHS point-source solve (--lattice, --nrhs) for profiling")
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "df64"])
     ap.add_argument("--links", type=int, default=18, choices=[18, 12])
     ap.add_argument("--nrhs", type=int, default=1)
@@ -815,6 +863,8 @@ def main():
     if args.workload == "operator":
         # one operator configuration alone (used for profiling): --lattice, --prec, --links, --nrhs
         return operator_only(args, torch, local_rank)
+    if args.workload == "propsolve":
+        return propsolve_only(args, torch, local_rank)
     if args.workload == "batch":
         res = batch_section(torch, local_rank, args.quick)
         if rank == 0:

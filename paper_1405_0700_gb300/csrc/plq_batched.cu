@@ -183,7 +183,10 @@ extern "C" plq_status plq_cg_solve_batched(plq_ctx **ctxs, int n, void **x, cons
             infos[k].n_reliable = res[k].n_reliable;
             infos[k].true_rel_residual = rel;
             infos[k].seconds = secs;
-            infos[k].hop_applications = 4.0 * res[k].iterations + 4.0 * (res[k].n_reliable + 1) + 2;
+            // inner: 4 per iteration, 2 per reliable update; FP64: bhat, 2 per residual
+            // check after the first (the first is free at x_e = 0), 2 for the check above
+            infos[k].hop_applications =
+                4.0 * res[k].iterations + 4.0 * res[k].n_reliable + (use_x0 ? 5.0 : 3.0);
         }
         if (st_k != PLQ_OK && status == PLQ_OK)
             status = set_error(st_k, "system %d: %s (residual %.3e after %d iterations)", k,

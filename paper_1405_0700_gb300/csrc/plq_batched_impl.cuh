@@ -55,6 +55,7 @@ struct BatchResult {
 enum Mode {
     M_SETUP0 = 0,  // |b|^2, x_e = 0
     M_SETUP1,      // bhat = b_e + kappa H_eo b_o
+    M_RES0,        // x_e = 0: s = bhat, |s|^2 (no operator; s also kept as sL)
     M_RES1,        // to = H_oe x_e                            (FP64)
     M_RES2,        // s = bhat - x_e + kappa^2 H_eo to, |s|^2   (FP64; s also kept as sL)
     M_RES3,        // toL = D_oe sL                            (inner, dagger)
@@ -67,7 +68,7 @@ enum Mode {
     M_IT5,         // x += alpha p, r -= alpha q, |r|^2 -> beta
     M_IT6,         // p = r + beta p
     M_ACC,         // x_e += xL (FP64)
-    M_FIN1,        // x_o = b_o + kappa H_oe x_e
+    M_FIN1,        // x_o = b_o + kappa H_oe x_e (H_oe x_e of the last check, kept in to)
     M_ZERO,        // zero source: x_o = 0
     M_DONE
 };
@@ -76,6 +77,7 @@ enum { BF_NAN = 1, BF_NOT_CONVERGED = 2 };
 
 struct SysRun {
     int mode, iter, nrel, first, flags, reduces;
+    int toe;    // to64 holds H_oe x_e of the current x_e
     double b2, s2, r2, rho, alpha, beta, last_rho, stop_r2, target2, sigma;
     double sc;  // power of two applied where the residual enters the inner precision
 };
@@ -283,20 +285,37 @@ __device__ double run_site(int mode, const BatchSystem &B, const SysRun &R, int 
         st<PLQ_F64>(B.bhat, Vh, i, acc);
         return 0.0;
     }
-    case M_RES1:
-    case M_FIN1: {
+    case M_RES0: {  // M_RES1/M_RES2 at x_e = 0 give s = bhat exactly
+        cx<double> bh[12];
+        cx<T> sl[12];
+        ld<PLQ_F64>(B.bhat, Vh, i, bh);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) sl[k] = {(T)(R.sc * bh[k].re), (T)(R.sc * bh[k].im)};
+        st<PLQ_F64>(B.s64, Vh, i, bh);
+        st<PL>(B.mpL, Vh, i, sl);  // mpL is free until the inner iteration starts
+        return norm12(bh);
+    }
+    case M_RES1: {
         cx<double> acc[12];
         hop_site<PLQ_F64, 18>(B.lat, B.g64, B.gb64, 1, false, B.xe, i, acc);
-        if (mode == M_FIN1) {
-            cx<double> b[12];
-            ld<PLQ_F64>(B.bo, Vh, i, b);
-#pragma unroll
-            for (int k = 0; k < 12; ++k)
-                acc[k] = {fma(B.kappa, acc[k].re, b[k].re), fma(B.kappa, acc[k].im, b[k].im)};
-            st<PLQ_F64>(B.xo, Vh, i, acc);
+        st<PLQ_F64>(B.to64, Vh, i, acc);
+        return 0.0;
+    }
+    case M_FIN1: {
+        // H_oe x_e of the final x_e was stored by its residual check (M_RES1),
+        // so x_o takes the same FP64 values without a second application; after
+        // a check at x_e = 0 (M_RES0) it is zero
+        cx<double> acc[12], b[12];
+        if (R.toe) {
+            ld<PLQ_F64>(B.to64, Vh, i, acc);
         } else {
-            st<PLQ_F64>(B.to64, Vh, i, acc);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k] = {0.0, 0.0};
         }
+        ld<PLQ_F64>(B.bo, Vh, i, b);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = {fma(B.kappa, acc[k].re, b[k].re), fma(B.kappa, acc[k].im, b[k].im)};
+        st<PLQ_F64>(B.xo, Vh, i, acc);
         return 0.0;
     }
     case M_RES2: {
@@ -421,7 +440,8 @@ __device__ double run_site(int mode, const BatchSystem &B, const SysRun &R, int 
 }
 
 __device__ __forceinline__ bool reduces(int mode) {
-    return mode == M_SETUP0 || mode == M_RES2 || mode == M_RES4 || mode == M_IT2 || mode == M_IT5;
+    return mode == M_SETUP0 || mode == M_RES0 || mode == M_RES2 || mode == M_RES4 || mode == M_IT2 ||
+           mode == M_IT5;
 }
 
 // Deterministic state update after a phase, applied identically by every
@@ -436,8 +456,12 @@ __device__ inline void advance(SysRun &R, const BatchSystem &B, double v) {
         // magnitude sit in the inner precision's exponent range
         if (isfinite(v) && v > 0.0 && B.inner_scaled) R.sc = ldexp(1.0, -ilogb(sqrt(v)));
         break;
-    case M_SETUP1: R.mode = M_RES1; break;
-    case M_RES1: R.mode = M_RES2; break;
+    case M_SETUP1: R.mode = B.use_x0 ? M_RES1 : M_RES0; break;
+    case M_RES1:
+        R.toe = 1;
+        R.mode = M_RES2;
+        break;
+    case M_RES0:
     case M_RES2:
         R.s2 = v;
         if (!isfinite(v)) { R.flags |= BF_NAN; R.mode = M_FIN1; }
@@ -502,7 +526,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) batched_cg_kernel(BatchArgs a) {
     for (int s = threadIdx.x; s < ns; s += blockDim.x) {
         SysRun R;
         R.mode = M_SETUP0;
-        R.iter = R.nrel = R.flags = R.reduces = 0;
+        R.iter = R.nrel = R.flags = R.reduces = R.toe = 0;
         R.first = 1;
         R.b2 = R.s2 = R.r2 = R.rho = R.alpha = R.beta = R.last_rho = R.stop_r2 = R.target2 = 0.0;
         R.sigma = 0.5;

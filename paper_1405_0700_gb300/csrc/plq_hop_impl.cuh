@@ -563,6 +563,16 @@ __global__ void __maxnreg__(RT == 1 ? 80 : 168) hop_mrhs_kernel(const HopArgs a)
     const int plane = L.L[2] * (L.L[1] >> 1);
     const int zc = a.zc;
     const int nblk = (L.Vh + S - 1) / S;
+    if (a.st != nullptr) {
+        // every right-hand side frozen (a solver's iterations past convergence):
+        // nothing to stage or compute; the reduction still counts this block
+        bool all_stopped = true;
+        for (int r = 0; r < n; ++r) all_stopped = all_stopped && a.st[r].stop;
+        if (all_stopped) {
+            if constexpr (NV > 0) grid_reduce(a.red, racc, blockDim.x);
+            return;
+        }
+    }
     for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
         __syncthreads();  // the previous site block is done with the shared links
         // stage: (site, direction) pairs

@@ -256,10 +256,21 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
         }
 
         const double delta = S.P == PLQ_F64 ? 0.0 : P.delta;
+        // tmp_o64 holds H_oe x_e of the current x_e (an FP64 residual check of the
+        // Wilson operator left it there); the final x_o and full residual reuse it
+        bool have_toe = false;
         for (;;) {
-            // (t64 is free until the final check; it holds the float-float fields)
-            st = df_res ? true_residual_df(S, dfsh.data(), s64, tmp_o64, t64, bhat, xe, s2.data())
-                        : true_residual(S, s64, tmp_o64, bhat, xe, s2.data());
+            if (first && !P.use_x0) {
+                // x_e = 0: s = bhat exactly, without applying the operator
+                have_toe = false;
+                st = blas_copy_convert(S.N, s64, PLQ_F64, bhat, PLQ_F64, s);
+                if (st == PLQ_OK) st = norm2_64(S, s64, s2.data());
+            } else {
+                // (t64 is free until the final check; it holds the float-float fields)
+                st = df_res ? true_residual_df(S, dfsh.data(), s64, tmp_o64, t64, bhat, xe, s2.data())
+                            : true_residual(S, s64, tmp_o64, bhat, xe, s2.data());
+                have_toe = !df_res && S.nu == 0.0;
+            }
             if (st != PLQ_OK) break;
             bool all_done = true;
             for (int r = 0; r < n; ++r) {
@@ -420,6 +431,10 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
             if ((st = df_hop(c, 1, tmp_o64, t64, tmp_o64, kappa, 0.0, 1.0, n, s)) != PLQ_OK) break;
             if ((st = df_join(S.N, n, dfsh.data(), xo, tmp_o64, s)) != PLQ_OK) break;
             S.hops += 1;
+        } else if (have_toe) {
+            // the same FP64 values as the operator's xpay epilogue: fma(kappa, H_oe x_e, b_o)
+            if ((st = blas_copy_convert(S.N, xo, PLQ_F64, tmp_o64, PLQ_F64, s)) != PLQ_OK) break;
+            if ((st = blas_xpay64(S.N, bo, kappa, xo, s)) != PLQ_OK) break;
         } else if ((st = hop(S, PLQ_F64, 1, xo, xe, EPI_XPAY, 0, bo, kappa)) != PLQ_OK) {
             break;
         }
@@ -431,9 +446,12 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
             break;
         if ((st = blas_xpay64(S.N, be, -1.0, t64, s)) != PLQ_OK) break;
         if ((st = norm2_64(S, t64, re.data())) != PLQ_OK) break;
-        if ((st = hop(S, PLQ_F64, 1, tmp_o64, xe, EPI_XPAY, 0, xo, -kappa, FIN_NONE, nullptr, false, tw_diag(S))) !=
-            PLQ_OK)
+        if (have_toe) {  // (M x)_o = x_o - kappa H_oe x_e, H_oe x_e still in tmp_o64
+            if ((st = blas_xpay64(S.N, xo, -kappa, tmp_o64, s)) != PLQ_OK) break;
+        } else if ((st = hop(S, PLQ_F64, 1, tmp_o64, xe, EPI_XPAY, 0, xo, -kappa, FIN_NONE, nullptr, false,
+                             tw_diag(S))) != PLQ_OK) {
             break;
+        }
         if ((st = blas_xpay64(S.N, bo, -1.0, tmp_o64, s)) != PLQ_OK) break;
         if ((st = norm2_64(S, tmp_o64, ro.data())) != PLQ_OK) break;
         for (int r = 0; r < n; ++r) {

@@ -56,6 +56,52 @@ def test_multi_rhs_48c96_twelve_rhs_sampled_sites():
             torch.cuda.empty_cache()
 
 
+def test_propagator_48c96_point_sources_sampled_residual():
+    """The propagator workload's solve (48^3 x 96, eps 0.25, seed 4, kappa 0.121, point
+    sources, FP32 inner iterations with 12-real links, FP64 residual checks, true
+    residual 1e-10) for two of its spin x colour columns, solved together.  The returned
+    x is checked with the C oracle's Eq. (1) on sampled sites, the source site and its
+    eight neighbours among them: at every site |b - M x| must stay below the global bound
+    1e-10 |b| (a full FP64 CPU solve at this size would take hours)."""
+    dims = (96, 48, 48, 48)
+    n, kappa = 2, 0.121
+    cols = (0, 7)  # spin 0 colour 0, spin 2 colour 1
+    U = S.gauge_field(dims, 0.25, 4)
+    V = S.volume(dims)
+    T, Lx, Ly, Lz = dims
+    # the origin, its 8 neighbours (lexicographic site = ((t Lz + z) Ly + y) Lx + x) and random sites
+    near = [0, 1, Lx - 1, Lx, (Ly - 1) * Lx, Lx * Ly, (Lz - 1) * Lx * Ly, Lx * Ly * Lz, (T - 1) * Lx * Ly * Lz]
+    rng = np.random.default_rng(8)
+    sites = np.concatenate([near, rng.integers(0, V, 1200)]).astype(np.int64)
+    with Context(dims) as ctx:
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        ctx.autotune(F32, n)
+        b = torch.zeros(n * V * 24, dtype=torch.float64, device="cuda")
+        for r, c in enumerate(cols):
+            b[r * V * 24 + 2 * c] = 1.0
+        bd = ctx.empty_full(F64, n)
+        ctx.pack_spinor(bd, b, F64, n)
+        del b
+        x = ctx.empty_full(F64, n)
+        infos = ctx.cg_solve_multi(x, bd, kappa, n, tol=1e-10, inner_prec=F32, maxit=3000)
+        del bd
+        back = torch.empty(n * V * 24, dtype=torch.float64, device="cuda")
+        ctx.unpack_spinor(back, x, F64, n)
+        del x
+        for r, c in enumerate(cols):
+            assert infos[r].true_rel_residual <= 1e-10, infos[r].as_dict()
+            xr = back[r * V * 24:(r + 1) * V * 24].cpu().numpy().view(np.complex128).reshape(T, Lz, Ly, Lx, 4, 3)
+            mx = xr.reshape(V, 4, 3)[sites] - kappa * C.hopping_sites(U, xr, sites)
+            bs = np.zeros((len(sites), 4, 3), dtype=np.complex128)
+            bs[0, c // 3, c % 3] = 1.0  # sites[0] is the origin
+            res = np.abs(bs - mx).max()
+            assert res <= 1e-10, (r, c, res)
+            # the solution is not trivially small where the source sits
+            assert np.abs(xr[0, 0, 0, 0, c // 3, c % 3]) > 0.5
+        torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("inner,residual_prec", [(F32, F64), (F16, DF64)])
 def test_mixed_cg_24c48_benchmark_configuration(inner, residual_prec):
     """The solver workload (24^3 x 48, eps 0.3, seed 3, kappa 0.120, true residual 1e-10),

@@ -457,13 +457,47 @@ __device__ void grid_reduce(const Reduce &red, const RedAcc<NV, RT> &acc, int nc
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // each warp sums whole slots over the blocks, its `active` lanes striding
-    // by `active` (a partial last warp must still visit every block)
-    for (int t = warp; t < slots; t += nw) {
-        double s = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += active) s += __ldcg(red.partials + (size_t)b * kPartialSlots + t);
-        s = warp_sum(s, lane, active);
-        if (lane == 0) tots[t] = s;
+    // The last block sums every slot over the blocks in a fixed order.  With at
+    // least twice as many full warps as slots, g = (full warps) / slots warps
+    // share a slot: warp q of the slot's group takes blocks q*32 + lane,
+    // q*32 + lane + g*32, ... (four loads in flight per lane), then the group's
+    // warp sums are added in warp order.  Otherwise each warp takes whole slots,
+    // a partial last warp striding by its `active` lanes, so that every block is
+    // still visited.
+    const double *part = red.partials;
+    auto strided_sum = [&](int t, int first, int step) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int b = first;
+        for (; b + 3 * step < (int)gridDim.x; b += 4 * step) {
+            s0 += __ldcg(part + (size_t)b * kPartialSlots + t);
+            s1 += __ldcg(part + (size_t)(b + step) * kPartialSlots + t);
+            s2 += __ldcg(part + (size_t)(b + 2 * step) * kPartialSlots + t);
+            s3 += __ldcg(part + (size_t)(b + 3 * step) * kPartialSlots + t);
+        }
+        for (; b < (int)gridDim.x; b += step) s0 += __ldcg(part + (size_t)b * kPartialSlots + t);
+        return (s0 + s1) + (s2 + s3);
+    };
+    const int nfull = nthr >> 5;
+    const int g = nfull >= 2 * slots ? nfull / slots : 1;
+    if (g > 1) {
+        const int t = warp / g, q = warp % g;
+        if (warp < slots * g) {  // full warps only: slots * g <= nfull
+            double s = strided_sum(t, q * 32 + lane, g * 32);
+            s = warp_sum(s, lane, active);
+            if (lane == 0) slot[t * g + q] = s;  // slot[] is free again
+        }
+        __syncthreads();
+        if (tid < slots) {
+            double s = 0.0;
+            for (int k = 0; k < g; ++k) s += slot[tid * g + k];
+            tots[tid] = s;
+        }
+    } else {
+        for (int t = warp; t < slots; t += nw) {
+            double s = strided_sum(t, lane, active);
+            s = warp_sum(s, lane, active);
+            if (lane == 0) tots[t] = s;
+        }
     }
     __syncthreads();
     if (tid < n) {

@@ -926,6 +926,9 @@ plq_status dispatch_hop(const HopArgs &a, int epi, cudaStream_t s, int block) {
                             : launch_hop_t<P, R, EPI_XPAY, false, true>(a, s, block);
         return a.dagger ? launch_hop_t<P, R, EPI_XPAY, true>(a, s, block) : launch_hop_t<P, R, EPI_XPAY, false>(a, s, block);
     case EPI_XPAY_NORM:
+        if (tbl)
+            return a.dagger ? launch_hop_t<P, R, EPI_XPAY_NORM, true, true>(a, s, block)
+                            : launch_hop_t<P, R, EPI_XPAY_NORM, false, true>(a, s, block);
         return a.dagger ? launch_hop_t<P, R, EPI_XPAY_NORM, true>(a, s, block)
                         : launch_hop_t<P, R, EPI_XPAY_NORM, false>(a, s, block);
     case EPI_XPAY_DOTW:

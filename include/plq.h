@@ -125,8 +125,8 @@ typedef struct {
     int inner_prec;    /* PLQ_F64 (plain FP64 solve), PLQ_F32 or PLQ_F16 inner precision   */
     double delta;      /* reliable-update trigger: the FP64 residual is recomputed when the
                           inner residual fell by this factor since the last update;
-                          default 1e-3 for FP32, 1e-2 for FP16 inner solves (ignored when
-                          inner_prec == PLQ_F64)                                            */
+                          default 1e-4 for FP32 (1e-3 for BiCGstab), 1e-2 for FP16 inner
+                          solves (ignored when inner_prec == PLQ_F64)                       */
     int use_x0;        /* 1: x holds an initial guess on entry (resume); 0: start from 0   */
     int check_every;   /* inner iterations per host convergence poll, default 16           */
     double mu;         /* twisted mass: solve M_tm = 1 - kappa H + 2 i kappa mu gamma5

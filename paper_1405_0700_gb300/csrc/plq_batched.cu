@@ -24,7 +24,7 @@ extern "C" plq_status plq_cg_solve_batched(plq_ctx **ctxs, int n, void **x, cons
     const int inner = params ? params->inner_prec : PLQ_F64;
     const double delta = inner == PLQ_F64 ? 0.0
                                            : ((params && params->delta > 0) ? params->delta
-                                                                            : (inner == PLQ_F16 ? 1e-2 : 1e-3));
+                                                                            : (inner == PLQ_F16 ? 1e-2 : 1e-4));
     const int use_x0 = params ? params->use_x0 : 0;
     if (!valid_prec(inner)) return set_error(PLQ_ERR_ARG, "bad inner precision %d", inner);
     const int device = ctxs[0] ? ctxs[0]->device : -1;

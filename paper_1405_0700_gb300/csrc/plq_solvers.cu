@@ -56,10 +56,13 @@ plq_status parse(const plq_solver_params *p, Params *o) {
     o->maxit = (p && p->maxit > 0) ? p->maxit : 20000;
     o->inner = p ? p->inner_prec : PLQ_F64;
     // Default reliable-update trigger: FP64 work is expensive on this GPU, so
-    // the inner solve runs as far as its precision allows between updates
-    // (measured on 24^3 x 48: 1e-3 for FP32, 1e-2 for FP16 storage).
+    // the inner solve runs as far as its precision allows between updates.
+    // Measured on 24^3 x 48 (and 32^3 x 64 with 12 point sources): FP32 inner
+    // iterations keep the FP64 iteration count for any trigger down to 1e-5,
+    // and below 3e-4 the updates are set by the tolerance alone (3 instead of
+    // 4 at 1e-3); FP16 storage needs 1e-2 (1e-3 already costs iterations).
     const int inner = p ? p->inner_prec : PLQ_F64;
-    o->delta = (p && p->delta > 0) ? p->delta : (inner == PLQ_F16 ? 1e-2 : 1e-3);
+    o->delta = (p && p->delta > 0) ? p->delta : (inner == PLQ_F16 ? 1e-2 : 1e-4);
     o->use_x0 = p ? p->use_x0 : 0;
     o->k = (p && p->check_every > 0) ? p->check_every : 16;
     o->mu = p ? p->mu : 0.0;
@@ -125,6 +128,10 @@ plq_status solve_impl(plq_ctx *c, void *x, const void *b, double kappa, int n, c
     if (!std::isfinite(kappa)) return set_error(PLQ_ERR_ARG, "kappa not finite");
     Params P;
     PLQ_TRY(parse(pp, &P));
+    // BiCGstab restarts from each recomputed residual (defect correction), so a
+    // longer inner cycle costs it iterations: with FP32 inner iterations it keeps
+    // 1e-3 (24^3 x 48: 20 iterations at 1e-3, 22 at 1e-4)
+    if (method == SOLVER_BICGSTAB && P.inner == PLQ_F32 && !(pp && pp->delta > 0)) P.delta = 1e-3;
     if (!c->gauge[PLQ_F64].ptr) return set_error(PLQ_ERR_STATE, "solvers need the FP64 gauge copy");
     if (!c->gauge[P.inner].ptr) return set_error(PLQ_ERR_STATE, "no gauge copy for inner precision %d", P.inner);
     const bool df_res = P.residual == PLQ_DF64 && P.inner != PLQ_F64;

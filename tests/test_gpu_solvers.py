@@ -296,6 +296,47 @@ def test_batched_sources_of_any_magnitude():
         c.close()
 
 
+def test_batched_resume_from_a_given_x():
+    """use_x0 in the persistent launch: the first residual check then applies the
+    operator to the given x_e (not the x_e = 0 shortcut), and the final x_o comes
+    from the H_oe x_e of the last check.  Resuming from a converged x returns it
+    after one check and no iteration; resuming from a perturbed x converges again.
+    Each x is checked with the oracle's operator."""
+    from paper_1405_0700_gb300 import plq as P
+
+    specs = S.batch_solve_specs(n=3, sizes=((8, 4, 4, 4), (16, 8, 8, 8)))
+    ctxs, xs, bs, Us, srcs = [], [], [], [], []
+    for sp in specs:
+        U, b = S.gauge_and_spinor(sp["dims"], sp["eps"], sp["seed"])
+        ctx = Context(sp["dims"])
+        ctx.gauge_upload(U, 18, F64)
+        ctx.gauge_upload(U, 12, F32)
+        ctxs.append(ctx)
+        bs.append(ctx.to_device(b, F64))
+        xs.append(ctx.empty_full(F64))
+        Us.append(U)
+        srcs.append(b)
+    kappas = [sp["kappa"] for sp in specs]
+    P.cg_solve_batched(ctxs, xs, bs, kappas, inner_prec=F32)
+    infos, _ = P.cg_solve_batched(ctxs, xs, bs, kappas, inner_prec=F32, use_x0=True)
+    for k in range(len(specs)):
+        assert infos[k].iterations == 0, infos[k].as_dict()
+        res = oracle_residual(Us[k], srcs[k], ctxs[k].to_host(xs[k], F64), kappas[k])
+        assert res <= 1e-10, (k, res)
+        assert abs(infos[k].true_rel_residual - res) < 1e-11
+    # perturb every x (both parities) and resume
+    for k, sp in enumerate(specs):
+        noise = S.gaussian_spinor(sp["dims"], 900 + k) * 1e-3
+        xs[k] = ctxs[k].to_device(ctxs[k].to_host(xs[k], F64) + noise, F64)
+    infos, _ = P.cg_solve_batched(ctxs, xs, bs, kappas, inner_prec=F32, use_x0=True)
+    for k in range(len(specs)):
+        assert infos[k].iterations > 0
+        res = oracle_residual(Us[k], srcs[k], ctxs[k].to_host(xs[k], F64), kappas[k])
+        assert res <= 1e-10, (k, res, infos[k].as_dict())
+    for c in ctxs:
+        c.close()
+
+
 @pytest.mark.parametrize("inner", [F64, F16])
 def test_batched_inner_precisions(inner):
     from paper_1405_0700_gb300 import plq as P

@@ -15,6 +15,8 @@ machines", Sec. 2):
   theta+_mu(x) = (1 - gamma_mu) phi(x) and theta-_mu(x) = U_mu(x)^dagger
   (1 + gamma_mu) phi(x), psi(x) = sum_mu [U_mu(x) theta+_mu(x + mu) +
   theta-_mu(x - mu)].  Used to pin Eq. (1) against Eq. (2).
+* ``link_spinor_product``: psi(i) = U(i) phi(i), the kernel of the paper's
+  prefetch experiment (Sec. 2.2).
 * The Wilson operator M = 1 - kappa*H, its even-odd Schur complement
   Mhat = 1 - kappa^2 H_eo H_oe, and textbook CG (on Mhat^dagger Mhat) and
   BiCGstab (on Mhat) solvers.  The paper names no solver and no normalisation;
@@ -419,3 +421,24 @@ def brute_force_hopping_dense(U, t_bc=-1):
                         D[12 * s:12 * s + 12, 12 * jf:12 * jf + 12] += sign_f * np.kron(ONE4 - GAMMA[mu], Ux)
                         D[12 * s:12 * s + 12, 12 * jb:12 * jb + 12] += sign_b * np.kron(ONE4 + GAMMA[mu], Ub.conj().T)
     return D
+
+
+# --------------------------------------------------------------------------
+# The link x spinor kernel of the prefetch experiment (Sec. 2.2)
+# --------------------------------------------------------------------------
+def link_spinor_product(U, phi):
+    """psi(i) = U(i) phi(i) for records i = 0 .. n-1: the kernel that the paper
+    isolates to measure prefetching and addressing (Sec. 2.2, overlap of
+    communication with computation: sequential access, access through an index
+    array x[i] and through a pointer array).  The access order decides only which
+    record a loop step reaches; each record's result is its own SU(3) matrix
+    applied to the colour vector of each of its four spin components.
+
+    U: (n, 3, 3) complex, phi: (n, 4, 3) complex; returns (n, 4, 3).  Written as a
+    loop over the 4 spin components of a per-record matrix-vector product."""
+    U = np.asarray(U, dtype=np.complex128)
+    phi = np.asarray(phi, dtype=np.complex128)
+    out = np.empty_like(phi)
+    for s in range(4):
+        out[:, s, :] = np.matmul(U, phi[:, s, :, None])[:, :, 0]
+    return out

@@ -37,7 +37,7 @@ def test_link_spinor_stream(mode, prec):
     rng = np.random.default_rng(7)
     Uc = S.su3_from_hermitian(rng.standard_normal((n, 3, 3)), rng.standard_normal((n, 3, 3)), 0.5)
     ph = rng.standard_normal((n, 4, 3)) + 1j * rng.standard_normal((n, 4, 3))
-    expect = np.einsum("nab,nsb->nsa", Uc, ph)
+    expect = W.link_spinor_product(Uc, ph)  # the oracle's kernel of the prefetch experiment
     dt = torch.float64 if prec == F64 else torch.float32
     U = torch.from_numpy(Uc.view(np.float64).reshape(n, 18)).to("cuda", dt).contiguous()
     P = torch.from_numpy(ph.view(np.float64).reshape(n, 24)).to("cuda", dt).contiguous()

@@ -176,3 +176,24 @@ def test_schur_dense_block_algebra():
     assert np.max(np.abs(Mhat - Mhat_blocks)) < 1e-14
     Mhat_dag = W.dense(lambda v: W.schur_dag(U, v, kappa), shape)[np.ix_(e, e)]
     assert np.max(np.abs(Mhat_dag - Mhat.conj().T)) < 1e-15
+
+
+def test_link_spinor_product_pins():
+    """The link x spinor kernel of the prefetch experiment (Sec. 2.2): brute force
+    on a few records, the identity link, and unitarity (|U v| = |v| for every spin
+    component's colour vector when U is in SU(3))."""
+    rng = np.random.default_rng(3)
+    n = 7
+    U = S.su3_from_hermitian(rng.standard_normal((n, 3, 3)), rng.standard_normal((n, 3, 3)), 0.7)
+    phi = rng.standard_normal((n, 4, 3)) + 1j * rng.standard_normal((n, 4, 3))
+    got = W.link_spinor_product(U, phi)
+    brute = np.zeros_like(phi)
+    for i in range(n):
+        for s in range(4):
+            for a in range(3):
+                for b in range(3):
+                    brute[i, s, a] += U[i, a, b] * phi[i, s, b]
+    assert np.max(np.abs(got - brute)) < 1e-14
+    eye = np.broadcast_to(np.eye(3, dtype=complex), (n, 3, 3))
+    assert np.array_equal(W.link_spinor_product(eye, phi), phi)
+    assert np.allclose(np.linalg.norm(got, axis=2), np.linalg.norm(phi, axis=2), rtol=1e-13, atol=0)
